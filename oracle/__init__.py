@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for SMS-MUSSELS -- TEST INFRASTRUCTURE, not product code.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It shares no code with the CUDA path.
+
+Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
+
+* fft2c / ifft2c ............ pinned (explicit DFT-matrix sums, unitarity)
+* caipi_ramp ................ pinned (integer shift == circular image roll)
+* forward / adjoint ......... pinned (dense DFT-matrix brute force at N=8,
+                              adjoint dot test, A = I special case)
+* hankel / hankel_adjoint ... pinned (entrywise definition, dot test)
+* gram ...................... pinned (trace closed form, PSD, rank bounds)
+* irls_weight ............... pinned (W^2 (G + eps I) = I)
+* nullspace_weight .......... pinned (projector, annihilates a low-rank H)
+* penalty ................... pinned (brute-force sum, W = I closed form,
+                              periodic-FFT agreement on interior pixels)
+* cg ........................ pinned (exact solve in n steps, small SPD)
+* reconstruct ............... pinned (exact recovery with full sampling;
+                              slice-phase equivariance; noiseless recovery)
+"""
+from .smsm_oracle import *  # noqa: F401,F403
+from .smsm_oracle import (DEFAULT_PARAMS, adjoint, caipi_ramp, cg, fft2c, forward, gram,  # noqa: F401
+                          hankel, hankel_adjoint, ifft2c, irls_weight, magnitude, make_data,
+                          normal, nrmse, nullspace_weight, penalty, reconstruct, shot_lines,
+                          vdot)
