@@ -1,0 +1,183 @@
+/*
+ * smsm.h -- C ABI of the GB300-native SMS-MUSSELS reconstruction library.
+ *
+ * SMS-MUSSELS (Mani et al., arXiv 1901.01893) recovers the slice-unfolded,
+ * per-shot k-space of a simultaneous-multislice (blipped-CAIPI) multi-shot
+ * diffusion acquisition by minimising (Eq. 10)
+ *
+ *     || A(m) - y ||^2  +  lambda * sum_l || H_l(m) ||_*
+ *
+ * where A is the SENSE/CAIPI forward model of Fig. 1 and H_l is the block
+ * Hankel matrix of slice l's shot k-spaces (Eqs. 8-9).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller, C-contiguous,
+ *    16-byte aligned, complex values interleaved (re, im).  complex64 = two
+ *    float32, complex128 = two float64.  The x (readout, kx) index is fastest.
+ *  - k-space is centred: index n has DC at n = N/2; the DFT is unitary.
+ *  - L = mb (slices), Ns = shots, Nc = coils, N = nx = ny, r = filter,
+ *    C = Ns*r*r (columns of H_l), P = (N-r+1)^2 (VALID patch origins).
+ *  - Unknown x: [L][Ns][N][N] complex64, per-shot k-space of each slice.
+ *    Data y: [Ns][Nc][N/Ns][N] complex64; shot i holds the lines
+ *    n = m*Ns + i, m = 0..N/Ns-1 (Eq. 2, 0-based).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  Only the report of smsm_reconstruct needs a sync, which
+ *    that call performs itself when `report` is non-NULL.
+ *  - Errors never abort: every call returns an smsm_status; smsm_last_error()
+ *    returns a message for the calling thread's last failure.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the
+ *    caller (its workspace is shared by all its calls).
+ */
+#ifndef SMSM_H
+#define SMSM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct smsm_plan_s* smsm_plan_t;
+
+typedef enum {
+  SMSM_OK = 0,
+  SMSM_ERR_ARG = 1,       /* bad size, NULL or misaligned pointer, unsupported shape */
+  SMSM_ERR_CUDA = 2,      /* a CUDA runtime call failed (message has the CUDA error) */
+  SMSM_ERR_NOMEM = 3,     /* device allocation failed while building the plan */
+  SMSM_ERR_DIVERGED = 4,  /* a CG scalar became NaN/Inf (reported via smsm_report) */
+  SMSM_ERR_NOT_PD = 5,    /* <p, N p> <= 0 in CG: system not positive definite */
+  SMSM_ERR_TIMEOUT = 6,   /* reserved: a bounded device wait gave up */
+  SMSM_ERR_STATE = 7      /* call out of order, e.g. no coil maps set yet */
+} smsm_status;
+
+typedef enum { SMSM_MODE_IRLS = 0, SMSM_MODE_NULLSPACE = 1 } smsm_mode;
+
+/* Plan options (all zero = defaults). */
+typedef struct {
+  int caipi_div;   /* CAIPI FOV shift is FOV/caipi_div per slice index; 0 -> mb (Eq. 1) */
+  int reserved[7];
+} smsm_opts;
+
+/*
+ * Solver parameters.  The paper minimises Eq. 10 with an augmented-Lagrangian
+ * scheme whose listing is in another paper; this library minimises the same
+ * cost by IRLS: at outer iteration k the nuclear norm is majorised with
+ * W_l = (G_l + eps_k I)^(-1/2), G_l = H_l^H H_l, and cg_iters steps of CG solve
+ *     (A^H A + lambda P_W) x = A^H y,   P_W(x)_l = H_l^*(H_l(x_l) W_l).
+ * eps_1 = eps0_rel * max_l s_max(G_l); eps_k = max(eps_{k-1}/eta, eps_min_rel*eps_1).
+ * NULLSPACE mode instead uses W_l = projector onto the C - rank smallest
+ * eigenvectors of G_l (one rank for every slice).
+ */
+typedef struct {
+  double lambda;      /* penalty weight in the normal equations (default 1e-2) */
+  double eps0_rel;    /* default 1e-2 */
+  double eta;         /* default 1.5 */
+  double eps_min_rel; /* default 1e-4 */
+  int outer_iters;    /* K, default 10, at most SMSM_MAX_OUTER */
+  int cg_iters;       /* J, default 10 */
+  int mode;           /* smsm_mode */
+  int rank;           /* NULLSPACE rank, 0 < rank < C */
+  int warm;           /* 1: x holds the starting point on entry; 0: start from A^H y */
+  int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 15 */
+  int reserved[6];
+} smsm_params;
+
+#define SMSM_MAX_OUTER 128
+
+/* Per-call report, filled after the call's work has finished (host memory). */
+typedef struct {
+  int status;                           /* smsm_status of the device-side checks */
+  int outer_done;                       /* outer iterations run */
+  double eps[SMSM_MAX_OUTER];           /* eps_k (IRLS) */
+  double rr_start[SMSM_MAX_OUTER];      /* ||r||^2 at the start of outer k's CG */
+  double rr_end[SMSM_MAX_OUTER];        /* ||r||^2 after its cg_iters steps */
+  int sweeps[SMSM_MAX_OUTER];           /* Jacobi sweeps used (max over slices) */
+  float elapsed_ms;                     /* device time of the solve (CUDA events) */
+} smsm_report;
+
+/* Fill *p with the defaults listed above. */
+void smsm_default_params(smsm_params* p);
+
+/*
+ * Create a plan for one slice-group geometry (the problem statement around
+ * Eq. 10: y of size N1 x N2/Ns x Nc x Ns, L simultaneously excited slices,
+ * filter (phase-support) size r of Eq. 8).
+ *   mb     L >= 1         shots  Ns >= 1, N % Ns == 0
+ *   coils  Nc >= 1        nx, ny equal, even, of the form 2^a 3^b, 16..512
+ *   filter r, 1 <= r <= N/2; C = Ns*r*r <= 320
+ * Allocates all device workspace (caller's current device).  On failure *out
+ * is NULL.
+ */
+smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils, int nx, int ny, int filter,
+                      const smsm_opts* opts /* nullable */);
+
+/* Release the plan and its device memory (NULL is a no-op). */
+smsm_status smsm_plan_destroy(smsm_plan_t plan);
+
+/* Bytes of device memory the plan holds. */
+size_t smsm_plan_workspace_bytes(smsm_plan_t plan);
+
+/*
+ * Set the coil sensitivities S (Fig. 1 step (ii)): sens is [L][Nc][N][N]
+ * complex64, image domain.  The plan keeps its own copy (transposed for the
+ * column kernels), so `sens` may be freed once the stream has passed this call.
+ */
+smsm_status smsm_plan_set_sens(smsm_plan_t plan, const void* sens, void* stream);
+
+/*
+ * y = A(x), Fig. 1 steps (i)-(v): inverse DFT, coil multiply, DFT, CAIPI phase
+ * exp(-j 2 pi l (n - N/2)/caipi_div) and slice sum (Eqs. 1, 3), shot mask.
+ *   phase == NULL: x is [L][Ns][N][N] per-shot k-space (the unknown of Eq. 10).
+ *   phase != NULL: x is [L][1][N][N] shared k-space and phase [L][Ns][N][N]
+ *                  complex64 is the image-domain shot phase phi_{l,i} (Eq. 4).
+ *   y: [Ns][Nc][N/Ns][N] complex64 (overwritten).
+ */
+smsm_status smsm_forward(smsm_plan_t plan, const void* x, const void* phase, void* y, void* stream);
+
+/* x = A^H(y), the adjoint of smsm_forward (same layouts; x overwritten). */
+smsm_status smsm_adjoint(smsm_plan_t plan, const void* y, const void* phase, void* x, void* stream);
+
+/*
+ * G_l = H_l^H H_l for every slice (Eqs. 8-9): x is [L][Ns][N][N] complex64,
+ * G is [L][C][C] complex128 (full Hermitian matrix, overwritten), with
+ * G[(i,p),(i',q)] = sum_{k in [0,N-r]^2} conj(x_i[k+p]) x_i'[k+q],
+ * column index (i,p) = i*r*r + py*r + px.
+ */
+smsm_status smsm_hankel_gram(smsm_plan_t plan, const void* x, void* G, void* stream);
+
+/*
+ * out = P_W(x): out_l = H_l^*(H_l(x_l) W_l), the annihilating-filter penalty
+ * (the gradient of ||H_l(x) W^(1/2)||_F^2 up to a factor 2).  W is
+ * [L][C][C] complex128, Hermitian (only that is assumed); x, out are
+ * [L][Ns][N][N] complex64 and must not alias.
+ */
+smsm_status smsm_apply_filters(smsm_plan_t plan, const void* W, const void* x, void* out,
+                               void* stream);
+
+/*
+ * The SMS-MUSSELS reconstruction (Eq. 10) by IRLS + CG (see smsm_params).
+ *   y: [Ns][Nc][N/Ns][N] complex64 measured data.
+ *   x: [L][Ns][N][N] complex64; input when params->warm, always the output.
+ * The whole solve runs on the device (captured once per plan and parameter
+ * set as a CUDA graph).  `report` (host, nullable) is filled after a stream
+ * sync; without it the call does not block.
+ */
+smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const smsm_params* params,
+                             smsm_report* report, void* stream);
+
+/*
+ * Centred unitary 2D DFT of `count` N x N complex64 images (Fig. 1 steps
+ * (i)/(iii)): inverse != 0 selects F^-1.  in and out may alias.
+ */
+smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, int inverse,
+                       void* stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* smsm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMSM_H */

@@ -1,0 +1,167 @@
+// Shared definitions of the SMS-MUSSELS CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/smsm.h"
+
+// ----------------------------------------------------------------------------
+// complex64 helpers (float2 = re, im)
+// ----------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return cmk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return cmk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return cmk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 conjf2(float2 a) { return cmk(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulcj(float2 a, float2 b) {
+  return cmk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc += a * b
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cfmacj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// ----------------------------------------------------------------------------
+// FFT descriptor: length n = prod(rad[0..np)), radices in {2, 3, 4}.
+// ----------------------------------------------------------------------------
+struct FftDesc {
+  int n;
+  int np;
+  int rad[12];
+};
+
+// ----------------------------------------------------------------------------
+// Device-side solver state (one per plan).
+// ----------------------------------------------------------------------------
+struct SolverState {
+  double eps;      // current eps_k
+  double eps0;     // eps_1
+  double eps_min;  // eps_min_rel * eps_1
+  int status;      // smsm_status set by device checks
+  int pad;
+};
+
+struct DevReport {
+  double eps[SMSM_MAX_OUTER];
+  double rr_start[SMSM_MAX_OUTER];
+  double rr_end[SMSM_MAX_OUTER];
+  int sweeps[SMSM_MAX_OUTER];
+};
+
+// Maximum sizes of this build.
+#define SMSM_MAX_C 320
+#define SMSM_MAX_N 512
+#define SMSM_MAX_SWEEPS 30
+#define SMSM_PART_MAX 8192  // capacity of each partial-sum array (doubles)
+
+struct smsm_plan_s {
+  int L, Ns, Nc, N, r, C, Cp /* C rounded up to even */, M, Ldiv, P1 /* N-r+1 */, R2 /* 2r-1 */;
+  int nband;  // pixels within r-1 of an edge
+  int dev;
+  FftDesc fN, fM;
+  float sN;   // (-1)^(N/2)/sqrt(N)
+  // tables (device)
+  float2 *twN, *twM, *tw_shot, *cph, *Etab;
+  // coil maps, transposed [L][Nc][x][y]
+  float2* sensT;
+  int has_sens;
+  // work buffers
+  float2 *hA, *hB;   // [L][Ns][N][N]
+  float2* yh;        // [Ns][Nc][N][M] (x-major)
+  float2* phaseT;    // [L][Ns][N][N] (x-major)
+  float2 *xs, *bv, *rv, *pv, *qv;  // solver vectors [L][Ns][N][N]
+  float2* ybuf;      // [Ns][Nc][M][N]
+  double2* G64;      // [L][C][C]
+  double2* Gpart;    // [L][nkx][C][C]
+  int gram_nkx;
+  float* eig;        // [L][Cp]
+  float4* rotlog;    // [L][SMSM_MAX_SWEEPS][Cp-1][Cp/2]
+  int* sweeps;       // [L]
+  float2 *V, *Wf;    // [L][C][C]
+  float2* wper;      // [L][Ns][Ns][R2*R2]
+  float2* wcls;      // [L][R2*R2][Ns][Ns][R2*R2]
+  float2* multT;     // [L][Ns][Ns][N(x)][N(y)]
+  double *part_pq_col, *part_pq_band, *part_rr;  // partial sums; part_rr has 2 banks
+  SolverState* st;
+  DevReport* rep;
+  size_t bytes;
+  // graph cache for smsm_reconstruct
+  cudaGraphExec_t gexec;
+  cudaStream_t cap_stream;
+  smsm_params gparams;
+  int has_graph;
+  cudaEvent_t ev0, ev1;
+};
+
+// ----------------------------------------------------------------------------
+// error reporting (host)
+// ----------------------------------------------------------------------------
+void smsm_set_error(const char* fmt, ...);
+
+#define SMSM_CUDA_TRY(call)                                                          \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      smsm_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                     __LINE__);                                                      \
+      return SMSM_ERR_CUDA;                                                          \
+    }                                                                                \
+  } while (0)
+
+#define SMSM_LAUNCH_CHECK(what)                                                        \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) {                                                           \
+      smsm_set_error("launch of %s failed: %s", what, cudaGetErrorString(e_));         \
+      return SMSM_ERR_CUDA;                                                            \
+    }                                                                                  \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// launchers implemented in the .cu files (all enqueue on `s`, return status)
+// ----------------------------------------------------------------------------
+// operators.cu
+smsm_status launch_transpose(const float2* in, float2* out, int nb, int rows, int cols, cudaStream_t s);
+smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
+                                int inverse, cudaStream_t s);
+smsm_status launch_rowfft_in_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
+                               int inverse, cudaStream_t s);
+enum ColMode { COL_FWD = 0, COL_ADJ = 1, COL_NORMAL = 2, COL_PEN = 3 };
+smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const float2* in, float2* out,
+                       const float2* phaseT, const float2* multT, float lambda, double* dot_part,
+                       cudaStream_t s);
+// hankel.cu
+smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
+smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s);
+smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, float scale, double* dot_part,
+                        cudaStream_t s);
+smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s);
+// eig.cu
+smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
+                               cudaStream_t s);
+smsm_status eig_init_attrs(int Cp);
+size_t eig_jacobi_smem(int Cp);
+smsm_status operators_init_attrs();
+size_t smsm_col_smem_bytes(const smsm_plan_s* P);
+int band_blocks(const smsm_plan_s* P);
+// solver.cu
+int vec_blocks(const smsm_plan_s* P);
+smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
+                               smsm_report* report, cudaStream_t s);
+smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
+                             cudaStream_t s);

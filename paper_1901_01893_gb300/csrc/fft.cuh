@@ -1,0 +1,114 @@
+// Shared-memory batched FFT (mixed radix 2/3/4, Stockham autosort).
+//
+// Each pass with radix R over a length-n transform reads element j + r*n/R,
+// applies the twiddle w^(r*k*n/(s*R)) (k = j mod s, s = product of the
+// earlier radices, w = exp(-2 pi i/n)), does an R-point DFT, and writes
+// element (j/s)*s*R + k + r*s of the other buffer.  After all passes the
+// result is in natural order; no bit reversal is needed.  The twiddle table
+// holds exp(-2 pi i k/n), k < n, computed on the host in FP64.
+#pragma once
+#include "common.cuh"
+
+template <bool INV>
+__device__ __forceinline__ float2 tw_get(const float2* tw, int idx) {
+  float2 w = tw[idx];
+  return INV ? conjf2(w) : w;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* v) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* v) {
+  // forward: X1 = a0 - i a1 - a2 + i a3 ; inverse swaps the sign of i
+  float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  float2 s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+  // -i * d13 = (d13.y, -d13.x)
+  float2 rot = INV ? cmk(-d13.y, d13.x) : cmk(d13.y, -d13.x);
+  v[0] = cadd(s02, s13);
+  v[2] = csub(s02, s13);
+  v[1] = cadd(d02, rot);
+  v[3] = csub(d02, rot);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  // X1 = a0 - t1/2 -+ i (sqrt3/2) t2, X2 = a0 - t1/2 +- i (sqrt3/2) t2, t1 = a1+a2, t2 = a1-a2
+  const float h3 = 0.866025403784438647f;
+  float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+  float2 m = cmk(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+  // -i * h3 * t2 = (h3 t2.y, -h3 t2.x)
+  float2 j = INV ? cmk(-h3 * t2.y, h3 * t2.x) : cmk(h3 * t2.y, -h3 * t2.x);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, j);
+  v[2] = csub(m, j);
+}
+
+// Batched FFT of `nbatch` transforms of length d.n; transform b starts at
+// a + b*bstride (and b + b*bstride for the ping-pong buffer).  All threads
+// of the block take part; the routine ends with __syncthreads() after every
+// pass and returns the buffer that holds the result.  Unnormalised.
+template <bool INV>
+__device__ float2* fft_smem(float2* a, float2* b, int nbatch, int bstride, const FftDesc& d,
+                            const float2* tw) {
+  const int n = d.n;
+  int s = 1;
+  float2* src = a;
+  float2* dst = b;
+  for (int ps = 0; ps < d.np; ++ps) {
+    const int R = d.rad[ps];
+    const int nR = n / R;
+    const int tstep = n / (s * R);
+    const int ntask = nbatch * nR;
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+      const int bb = t / nR;
+      const int j = t - bb * nR;
+      const float2* S = src + bb * bstride;
+      float2* D = dst + bb * bstride;
+      const int k = j % s;
+      const int base = (j - k) * R + k;
+      float2 v[4];
+      if (R == 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = S[j + r * nR];
+        if (k) {
+#pragma unroll
+          for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], tw_get<INV>(tw, r * k * tstep));
+        }
+        dft4<INV>(v);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) D[base + r * s] = v[r];
+      } else if (R == 2) {
+        v[0] = S[j];
+        v[1] = S[j + nR];
+        if (k) v[1] = cmul(v[1], tw_get<INV>(tw, k * tstep));
+        dft2<INV>(v);
+        D[base] = v[0];
+        D[base + s] = v[1];
+      } else {  // R == 3
+#pragma unroll
+        for (int r = 0; r < 3; ++r) v[r] = S[j + r * nR];
+        if (k) {
+          v[1] = cmul(v[1], tw_get<INV>(tw, k * tstep));
+          v[2] = cmul(v[2], tw_get<INV>(tw, 2 * k * tstep));
+        }
+        dft3<INV>(v);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) D[base + r * s] = v[r];
+      }
+    }
+    __syncthreads();
+    float2* t = src;
+    src = dst;
+    dst = t;
+    s *= R;
+  }
+  return src;
+}
+
+// (-1)^n as a float
+__device__ __forceinline__ float sgn_par(int n) { return (n & 1) ? -1.f : 1.f; }

@@ -1,0 +1,268 @@
+// IRLS + CG solve of the SMS-MUSSELS cost (Eq. 10), entirely on the device.
+//
+// Outer iteration k: Gram of the current x -> Jacobi eigen-decomposition ->
+// W_k -> filters (periodic multipliers + border-class filters) -> J steps of
+// textbook CG on (A^H A + lambda P_W) x = A^H y from the current x.  All CG
+// scalars are reduced in FP64 from per-CTA partials in a fixed order, so
+// every CTA computes the same alpha/beta and runs are bit-reproducible; no
+// scalar ever goes back to the host, which lets the whole solve be captured
+// as one CUDA graph (replayed by later calls with the same parameters).
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+#define VEC_THREADS 256
+
+int vec_blocks(const smsm_plan_s* P) {
+  const size_t n2 = (size_t)P->L * P->Ns * P->N * P->N / 2;  // float4 = two complex
+  size_t b = (n2 + VEC_THREADS - 1) / VEC_THREADS;
+  if (b > 4 * 152) b = 4 * 152;
+  return (int)b;
+}
+
+// Sum of partial arrays a[0..na) + b[0..nb) in a fixed order; every thread
+// returns the same value.  `red` is VEC_THREADS doubles of shared memory.
+__device__ double sum_parts(const double* __restrict__ a, int na, const double* __restrict__ b, int nb, double* red) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < na; k += blockDim.x) s += a[k];
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s += b[k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ void block_partial(double v, double* red, double* out) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+__device__ __forceinline__ double norm2_4(float4 v) {
+  return (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+}
+
+// r = b - q; p = r; partial ||r||^2
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_init(const float4* __restrict__ b, const float4* __restrict__ q,
+                                                         float4* __restrict__ r, float4* __restrict__ p, size_t n4,
+                                                         double* __restrict__ part_rr) {
+  __shared__ double red[VEC_THREADS];
+  double s = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    float4 bv = b[e], qv = q[e];
+    float4 rv = make_float4(bv.x - qv.x, bv.y - qv.y, bv.z - qv.z, bv.w - qv.w);
+    r[e] = rv;
+    p[e] = rv;
+    s += norm2_4(rv);
+  }
+  block_partial(s, red, part_rr);
+}
+
+// alpha = <r,r>/<p,q>; x += alpha p; r -= alpha q; partial ||r||^2
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ x, float4* __restrict__ r,
+                                                           const float4* __restrict__ p, const float4* __restrict__ q,
+                                                           size_t n4, const double* __restrict__ pq_col, int ncol,
+                                                           const double* __restrict__ pq_band, int nband,
+                                                           const double* __restrict__ rr_in, int nrr,
+                                                           double* __restrict__ rr_out, SolverState* st) {
+  __shared__ double red[VEC_THREADS];
+  const double pq = sum_parts(pq_col, ncol, pq_band, nband, red);
+  const double rr = sum_parts(rr_in, nrr, nullptr, 0, red);
+  double alpha = rr / pq;
+  if (!(pq > 0.0) || !isfinite(alpha)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->status == 0)
+      st->status = isfinite(pq) ? SMSM_ERR_NOT_PD : SMSM_ERR_DIVERGED;
+    alpha = 0.0;
+  }
+  const float a = (float)alpha;
+  double s = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    float4 xv = x[e], rv = r[e];
+    const float4 pv = p[e], qv = q[e];
+    xv.x = fmaf(a, pv.x, xv.x);
+    xv.y = fmaf(a, pv.y, xv.y);
+    xv.z = fmaf(a, pv.z, xv.z);
+    xv.w = fmaf(a, pv.w, xv.w);
+    rv.x = fmaf(-a, qv.x, rv.x);
+    rv.y = fmaf(-a, qv.y, rv.y);
+    rv.z = fmaf(-a, qv.z, rv.z);
+    rv.w = fmaf(-a, qv.w, rv.w);
+    x[e] = xv;
+    r[e] = rv;
+    s += norm2_4(rv);
+  }
+  block_partial(s, red, rr_out);
+}
+
+// beta = rr_new/rr_old; p = r + beta p
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_pupdate(const float4* __restrict__ r, float4* __restrict__ p,
+                                                            size_t n4, const double* __restrict__ rr_new,
+                                                            const double* __restrict__ rr_old, int nrr) {
+  __shared__ double red[VEC_THREADS];
+  const double rn = sum_parts(rr_new, nrr, nullptr, 0, red);
+  const double ro = sum_parts(rr_old, nrr, nullptr, 0, red);
+  double beta = ro > 0.0 ? rn / ro : 0.0;
+  if (!isfinite(beta)) beta = 0.0;
+  const float bta = (float)beta;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 rv = r[e];
+    float4 pv = p[e];
+    pv.x = fmaf(bta, pv.x, rv.x);
+    pv.y = fmaf(bta, pv.y, rv.y);
+    pv.z = fmaf(bta, pv.z, rv.z);
+    pv.w = fmaf(bta, pv.w, rv.w);
+    p[e] = pv;
+  }
+}
+
+// which = 0: record ||r||^2 at the start of outer iteration `outer`; 1: at its end
+__global__ void k_record(DevReport* rep, int outer, int which, const double* __restrict__ rr, int nrr) {
+  __shared__ double red[VEC_THREADS];
+  const double a = sum_parts(rr, nrr, nullptr, 0, red);
+  if (threadIdx.x == 0 && outer < SMSM_MAX_OUTER) {
+    if (which == 0)
+      rep->rr_start[outer] = a;
+    else
+      rep->rr_end[outer] = a;
+  }
+}
+
+__global__ void k_reset_state(SolverState* st) {
+  st->status = 0;
+  st->eps = 0.0;
+  st->eps0 = 0.0;
+  st->eps_min = 0.0;
+}
+
+// q = (A^H A + lambda P_W) v.  With with_dots, the per-CTA partials of
+// Re<v, q> go to part_pq_col (column stage, image domain, Parseval) and
+// part_pq_band (border correction).
+smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
+                             cudaStream_t s) {
+  const int B = P->L * P->Ns;
+  smsm_status st;
+  if ((st = launch_rowfft_out_T(P, v, P->hA, B, P->N, 1, s))) return st;
+  if ((st = launch_col(P, COL_NORMAL, 0, P->hA, P->hB, nullptr, lambda != 0.f ? P->multT : nullptr, lambda,
+                       with_dots ? P->part_pq_col : nullptr, s)))
+    return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, q, B, P->N, 0, s))) return st;
+  if (lambda != 0.f) {
+    if ((st = launch_band(P, v, q, lambda, with_dots ? P->part_pq_band : nullptr, s))) return st;
+  } else if (with_dots) {
+    SMSM_CUDA_TRY(cudaMemsetAsync(P->part_pq_band, 0, sizeof(double) * band_blocks(P), s));
+  }
+  return SMSM_OK;
+}
+
+static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s) {
+  smsm_status st;
+  const int B = P->L * P->Ns;
+  const size_t n4 = (size_t)B * P->N * P->N / 2;
+  const int nvb = vec_blocks(P);
+  const int nbb = band_blocks(P);
+  const float lam = (float)prm->lambda;
+  double* rr0 = P->part_rr;
+  double* rr1 = P->part_rr + SMSM_PART_MAX;
+  k_reset_state<<<1, 1, 0, s>>>(P->st);
+  SMSM_LAUNCH_CHECK("k_reset_state");
+  // b = A^H y
+  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, P->Ns * P->Nc, P->M, 1, s))) return st;
+  if ((st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s))) return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, B, P->N, 0, s))) return st;
+  if (!prm->warm) SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)B * P->N * P->N,
+                                                cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < prm->outer_iters; ++k) {
+    if ((st = launch_gram(P, P->xs, P->G64, s))) return st;
+    if ((st = launch_eig_weights(P, P->G64, k, prm, s))) return st;
+    if ((st = launch_filters(P, P->Wf, s))) return st;
+    if ((st = apply_normal_pen(P, P->xs, P->qv, lam, 0, s))) return st;
+    k_cg_init<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv,
+                                          (float4*)P->pv, n4, rr0);
+    SMSM_LAUNCH_CHECK("k_cg_init");
+    k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 0, rr0, nvb);
+    SMSM_LAUNCH_CHECK("k_record");
+    for (int j = 0; j < prm->cg_iters; ++j) {
+      double* rin = (j & 1) ? rr1 : rr0;
+      double* rout = (j & 1) ? rr0 : rr1;
+      if ((st = apply_normal_pen(P, P->pv, P->qv, lam, 1, s))) return st;
+      k_cg_update<<<nvb, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
+                                              (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
+                                              lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
+      SMSM_LAUNCH_CHECK("k_cg_update");
+      k_cg_pupdate<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
+      SMSM_LAUNCH_CHECK("k_cg_pupdate");
+    }
+    double* rend = (prm->cg_iters & 1) ? rr1 : rr0;  // bank of the last write
+    k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 1, rend, nvb);
+    SMSM_LAUNCH_CHECK("k_record");
+  }
+  return SMSM_OK;
+}
+
+static bool same_params(const smsm_params* a, const smsm_params* b) { return memcmp(a, b, sizeof(*a)) == 0; }
+
+smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
+                               smsm_report* report, cudaStream_t s) {
+  const size_t nx = (size_t)P->L * P->Ns * P->N * P->N;
+  const size_t ny = (size_t)P->Ns * P->Nc * P->M * P->N;
+  if (!P->has_graph || !same_params(&P->gparams, prm)) {
+    if (P->has_graph) {
+      cudaGraphExecDestroy(P->gexec);
+      P->has_graph = 0;
+    }
+    cudaGraph_t g;
+    SMSM_CUDA_TRY(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
+    smsm_status st = enqueue_solve(P, prm, P->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(P->cap_stream, &g);
+    if (st) return st;
+    if (ce != cudaSuccess) {
+      smsm_set_error("stream capture of the solve failed: %s", cudaGetErrorString(ce));
+      return SMSM_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      smsm_set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+      return SMSM_ERR_CUDA;
+    }
+    P->gparams = *prm;
+    P->has_graph = 1;
+  }
+  SMSM_CUDA_TRY(cudaMemcpyAsync(P->ybuf, y, sizeof(float2) * ny, cudaMemcpyDeviceToDevice, s));
+  if (prm->warm) SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, x, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
+  SMSM_CUDA_TRY(cudaEventRecord(P->ev0, s));
+  SMSM_CUDA_TRY(cudaGraphLaunch(P->gexec, s));
+  SMSM_CUDA_TRY(cudaEventRecord(P->ev1, s));
+  SMSM_CUDA_TRY(cudaMemcpyAsync(x, P->xs, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
+  if (report) {
+    DevReport hr;
+    SolverState hs;
+    SMSM_CUDA_TRY(cudaMemcpyAsync(&hr, P->rep, sizeof(hr), cudaMemcpyDeviceToHost, s));
+    SMSM_CUDA_TRY(cudaMemcpyAsync(&hs, P->st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    SMSM_CUDA_TRY(cudaStreamSynchronize(s));
+    memset(report, 0, sizeof(*report));
+    report->status = hs.status;
+    report->outer_done = prm->outer_iters;
+    const int K = prm->outer_iters < SMSM_MAX_OUTER ? prm->outer_iters : SMSM_MAX_OUTER;
+    for (int k = 0; k < K; ++k) {
+      report->eps[k] = hr.eps[k];
+      report->rr_start[k] = hr.rr_start[k];
+      report->rr_end[k] = hr.rr_end[k];
+      report->sweeps[k] = hr.sweeps[k];
+    }
+    float ms = 0.f;
+    SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+    report->elapsed_ms = ms;
+  }
+  return SMSM_OK;
+}

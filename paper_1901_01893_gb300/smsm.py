@@ -1,0 +1,218 @@
+"""Thin ctypes binding of ``libsmsm.so`` (include/smsm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the reconstruction runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: if the library is missing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsmsm.so")
+
+SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
+SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
+SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
+SMSM_MAX_OUTER = 128
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("caipi_div", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("eps0_rel", ctypes.c_double), ("eta", ctypes.c_double),
+                ("eps_min_rel", ctypes.c_double), ("outer_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+                ("mode", ctypes.c_int), ("rank", ctypes.c_int), ("warm", ctypes.c_int),
+                ("max_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_done", ctypes.c_int),
+                ("eps", ctypes.c_double * SMSM_MAX_OUTER), ("rr_start", ctypes.c_double * SMSM_MAX_OUTER),
+                ("rr_end", ctypes.c_double * SMSM_MAX_OUTER), ("sweeps", ctypes.c_int * SMSM_MAX_OUTER),
+                ("elapsed_ms", ctypes.c_float)]
+
+
+class SmsmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"smsm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsmsm.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    L.smsm_plan.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, ctypes.POINTER(Opts)]
+    L.smsm_plan.restype = st
+    L.smsm_plan_destroy.argtypes = [vp]
+    L.smsm_plan_destroy.restype = st
+    L.smsm_plan_workspace_bytes.argtypes = [vp]
+    L.smsm_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.smsm_plan_set_sens.argtypes = [vp, vp, vp]
+    L.smsm_plan_set_sens.restype = st
+    for fn in ("smsm_forward", "smsm_adjoint"):
+        getattr(L, fn).argtypes = [vp, vp, vp, vp, vp]
+        getattr(L, fn).restype = st
+    L.smsm_hankel_gram.argtypes = [vp, vp, vp, vp]
+    L.smsm_hankel_gram.restype = st
+    L.smsm_apply_filters.argtypes = [vp, vp, vp, vp, vp]
+    L.smsm_apply_filters.restype = st
+    L.smsm_reconstruct.argtypes = [vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
+    L.smsm_reconstruct.restype = st
+    L.smsm_fft2c.argtypes = [vp, vp, vp, i, i, vp]
+    L.smsm_fft2c.restype = st
+    L.smsm_last_error.argtypes = []
+    L.smsm_last_error.restype = ctypes.c_char_p
+    L.smsm_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.smsm_default_params.restype = None
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != SMSM_OK:
+        raise SmsmError(status, lib().smsm_last_error().decode())
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().smsm_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+    return p
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t: torch.Tensor, shape, name: str, dtype=torch.complex64) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+class Plan:
+    """One slice-group geometry: smsm_plan(mb, shots, coils, N, N, filter)."""
+
+    def __init__(self, mb: int, shots: int, coils: int, n: int, filter: int, caipi_div: int = 0):
+        self.L, self.Ns, self.Nc, self.N, self.r = mb, shots, coils, n, filter
+        self.C = shots * filter * filter
+        self.M = n // shots if shots else 0
+        h = ctypes.c_void_p()
+        opts = Opts(caipi_div=caipi_div)
+        _check(lib().smsm_plan(ctypes.byref(h), mb, shots, coils, n, n, filter, ctypes.byref(opts)))
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().smsm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return lib().smsm_plan_workspace_bytes(self._h)
+
+    # shapes
+    @property
+    def x_shape(self):
+        return (self.L, self.Ns, self.N, self.N)
+
+    @property
+    def y_shape(self):
+        return (self.Ns, self.Nc, self.M, self.N)
+
+    def smsm_plan_set_sens(self, sens: torch.Tensor) -> None:
+        _check(lib().smsm_plan_set_sens(self._h, _dev(sens, (self.L, self.Nc, self.N, self.N), "sens"), _stream()))
+        self._sens = sens  # keep alive until the transpose has run
+
+    set_sens = smsm_plan_set_sens
+
+    def smsm_forward(self, x: torch.Tensor, phase: torch.Tensor | None = None, y: torch.Tensor | None = None):
+        xs = (self.L, 1 if phase is not None else self.Ns, self.N, self.N)
+        if y is None:
+            y = torch.empty(self.y_shape, dtype=torch.complex64, device=x.device)
+        pp = _dev(phase, self.x_shape, "phase") if phase is not None else None
+        _check(lib().smsm_forward(self._h, _dev(x, xs, "x"), pp, _dev(y, self.y_shape, "y"), _stream()))
+        return y
+
+    forward = smsm_forward
+
+    def smsm_adjoint(self, y: torch.Tensor, phase: torch.Tensor | None = None, x: torch.Tensor | None = None):
+        xs = (self.L, 1 if phase is not None else self.Ns, self.N, self.N)
+        if x is None:
+            x = torch.empty(xs, dtype=torch.complex64, device=y.device)
+        pp = _dev(phase, self.x_shape, "phase") if phase is not None else None
+        _check(lib().smsm_adjoint(self._h, _dev(y, self.y_shape, "y"), pp, _dev(x, xs, "x"), _stream()))
+        return x
+
+    adjoint = smsm_adjoint
+
+    def smsm_hankel_gram(self, x: torch.Tensor, G: torch.Tensor | None = None):
+        if G is None:
+            G = torch.empty((self.L, self.C, self.C), dtype=torch.complex128, device=x.device)
+        _check(lib().smsm_hankel_gram(self._h, _dev(x, self.x_shape, "x"),
+                                      _dev(G, (self.L, self.C, self.C), "G", torch.complex128), _stream()))
+        return G
+
+    hankel_gram = smsm_hankel_gram
+
+    def smsm_apply_filters(self, W: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None):
+        if out is None:
+            out = torch.empty(self.x_shape, dtype=torch.complex64, device=x.device)
+        _check(lib().smsm_apply_filters(self._h, _dev(W, (self.L, self.C, self.C), "W", torch.complex128),
+                                        _dev(x, self.x_shape, "x"), _dev(out, self.x_shape, "out"), _stream()))
+        return out
+
+    apply_filters = smsm_apply_filters
+
+    def smsm_reconstruct(self, y: torch.Tensor, x: torch.Tensor | None = None, params: Params | None = None,
+                         report: bool = True):
+        """Returns (x, Report or None).  x is the warm start when params.warm."""
+        if params is None:
+            params = default_params()
+        if x is None:
+            x = torch.empty(self.x_shape, dtype=torch.complex64, device=y.device)
+        rep = Report() if report else None
+        _check(lib().smsm_reconstruct(self._h, _dev(y, self.y_shape, "y"), _dev(x, self.x_shape, "x"),
+                                      ctypes.byref(params), ctypes.byref(rep) if rep is not None else None,
+                                      _stream()))
+        return x, rep
+
+    reconstruct = smsm_reconstruct
+
+    def smsm_fft2c(self, t: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
+        if out is None:
+            out = torch.empty_like(t)
+        count = t.numel() // (self.N * self.N)
+        _check(lib().smsm_fft2c(self._h, _dev(t, t.shape, "in"), _dev(out, t.shape, "out"), count,
+                                1 if inverse else 0, _stream()))
+        return out
+
+    fft2c = smsm_fft2c
