@@ -1,0 +1,372 @@
+"""Throughput of the SMS-MUSSELS reconstruction on GB300 (one JSON line on stdout).
+
+A step is one complete reconstruction of one slice group (every row of the
+hot path: A^H y, then K outer iterations of Gram -> Jacobi eigen-decomposition
+-> weights -> filters -> J CG steps of (A^H A + lambda P_W)) through the C ABI.
+The workload is the plain FP32 configuration: MB=2 slices, 4 interleaved
+shots, 32 coils, 128x128, filter 6x6, 20 outer x 15 CG iterations, seeded
+synthetic data (ellipse phantom, polynomial + band-limited shot phase, ring
+coil maps, SNR 30).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: slice groups are independent, so every rank reconstructs its own
+groups (replicas, weak scaling); the host only gathers the timings.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1901_01893_gb300 import synth  # noqa: E402
+
+METRIC = "slice-group recons/sec at NRMSE≤1e-3 vs FP64 oracle: learned+BF16+batched vs plain"
+UNIT = "slice-groups/s"
+WORKLOAD = "plain"
+LAM = 1e-2
+
+
+def workload_desc(c):
+    return (f"plain FP32 form: MB={c['L']} slices, {c['Ns']} interleaved shots, {c['Nc']} coils, "
+            f"{c['N']}x{c['N']}, filter {c['r']}x{c['r']}, {c['K']} outer x {c['J']} CG")
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample, extrapolated to one reconstruction)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(cfg, y, sens, reps=1):
+    """Time the oracle's pieces once each and extrapolate one full reconstruction:
+    T = T(A^H y) + K * (T(Gram + eigen/weights) + (J + 1) * T(one CG step))."""
+    import oracle as O
+
+    r, K, J = cfg["r"], cfg["K"], cfg["J"]
+    L = sens.shape[0]
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        b = O.adjoint(y, sens, L)
+        t1 = time.perf_counter()
+        G = O.gram(b, r)
+        W, s = O.irls_weight(G, 1e-2 * max(np.max(x) for x in np.linalg.eigvalsh(G)))
+        t2 = time.perf_counter()
+        q = O.normal(b, sens) + LAM * O.penalty(b, W, r)
+        _ = O.vdot(b, q)
+        t3 = time.perf_counter()
+        ts.append((t1 - t0, t2 - t1, t3 - t2))
+    ta = statistics.median(t[0] for t in ts)
+    tg = statistics.median(t[1] for t in ts)
+    tc = statistics.median(t[2] for t in ts)
+    total = ta + K * (tg + (J + 1) * tc)
+    sample = (f"oracle (NumPy FP64, explicit Hankel) on the same workload: timed A^H y, one Gram+eigh+W, one CG "
+              f"step (A^H A + lam P_W); extrapolated to {K} outer x ({J}+1) CG steps "
+              f"(sample {ta + tg + tc:.1f} s, full recon {total:.0f} s)")
+    return total, sample
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def make_host_inputs(cfg, seed):
+    g = synth.make_group(seed=seed, **{k: cfg[k] for k in ("L", "Ns", "Nc", "N", "field")})
+    return g
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+
+    cfg = dict(synth.CONFIGS[WORKLOAD])
+    g = make_host_inputs(cfg, cfg["seed"])
+    xt, y = O.make_data(g, cfg["snr"])
+    y = y / np.sqrt(np.mean(np.abs(y) ** 2))
+    for _ in range(args.warmup):
+        oracle_sample(cfg, y, g["sens"])
+    per = []
+    for _ in range(args.steps):
+        t, sample = oracle_sample(cfg, y, g["sens"])
+        per.append(t)
+    t = statistics.mean(per)
+    v = 1.0 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "form": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def stage_work(cfg):
+    """Algorithmic work of one launch (bracket) of each kernel class."""
+    L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
+    B, NN, M, C = L * Ns, N * N, N // Ns, Ns * r * r
+    P = (N - r + 1) ** 2
+    R2 = 2 * r - 1
+    nband = NN - (N - 2 * (r - 1)) ** 2
+    lg = np.log2
+    # column stage flops: per x line, per coil and slice-shot: coil x twiddle multiply
+    # (2 cmul/px), fold (1 cadd/px), forward + inverse M-point FFT (5 M log2 M each),
+    # CAIPI combine + back-projection (2 cmul/line), conj multiply-accumulate (2 cmul + cadd/px);
+    # plus the two N-point FFTs per slice-shot line and the Ns x Ns multiplier.
+    col_flops = N * (Nc * B * (6 * N * 2 + 2 * N + 2 * 5 * M * lg(M) + 2 * 8 * M + 6 * N * 2 + 2 * N)
+                     + B * 2 * 5 * N * lg(N) + B * Ns * 8 * N)
+    return {
+        "column": {"bytes": 8 * NN * (L * Nc + 2 * B + L * Ns * Ns), "flops": col_flops},
+        "rowfft_inv": {"bytes": 2 * 8 * B * NN, "flops": B * N * 5 * N * lg(N)},
+        "rowfft_fwd": {"bytes": 2 * 8 * B * NN, "flops": B * N * 5 * N * lg(N)},
+        "band": {"bytes": 8 * 2 * L * Ns * nband, "flops": 8 * 2 * L * nband * Ns * Ns * R2 * R2},
+        "cg": {"bytes": 9 * 8 * B * NN, "flops": 10 * B * NN},
+        "gram": {"bytes": 8 * B * NN, "flops": 8 * L * P * C * (C + 1) / 2},
+        "eig": {"bytes": 16 * L * C * C, "flops": None},
+    }
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1901_01893_gb300 import _build
+
+    _build.build()
+    from paper_1901_01893_gb300 import smsm
+
+    cfg = dict(synth.CONFIGS[WORKLOAD])
+    L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
+    seed = cfg["seed"] + 1000 * rank
+    g = make_host_inputs(cfg, seed)
+
+    plan = smsm.Plan(L, Ns, Nc, N, r)
+    c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(dev)  # noqa: E731
+    plan.set_sens(c64(g["sens"]))
+    # synthesis on the GPU: x_rho = F_c(rho); y = A(x_rho; phi) + noise at SNR 30; RMS(y) = 1
+    xr = plan.fft2c(c64(g["rho"][:, None]))
+    yc = plan.forward(xr, phase=c64(g["phase"]))
+    nz = c64(g["noise"])
+    y = yc + nz * (torch.linalg.vector_norm(yc) / (cfg["snr"] * torch.linalg.vector_norm(nz)))
+    y = (y / torch.sqrt(torch.mean(torch.abs(y) ** 2))).contiguous()
+    x = torch.empty(plan.x_shape, dtype=torch.complex64, device=dev)
+
+    allmask = (1 << len(smsm.STAGES)) - 1
+    prm = smsm.default_params(lam=LAM, outer_iters=cfg["K"], cg_iters=cfg["J"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up; the first one times every kernel class to find the dominant one
+    prm.timing = allmask
+    _, rep = plan.reconstruct(y, x=x, params=prm)
+    stages_all = {smsm.STAGES[k]: rep.stage_ms[k] for k in range(len(smsm.STAGES))}
+    dominant = max(stages_all, key=stages_all.get)
+    prm.timing = 1 << smsm.STAGE[dominant]
+    for _ in range(max(0, args.warmup - 1)):
+        plan.reconstruct(y, x=x, params=prm)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dom_ms, dom_n, launches = 0.0, 0, 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()  # L2 (129 MB) flushed before every step, outside the step's events
+            ev[k][0].record()
+            _, rep = plan.reconstruct(y, x=x, params=prm)
+            ev[k][1].record()
+            dom_ms += rep.stage_ms[smsm.STAGE[dominant]]
+            dom_n += rep.stage_launches[smsm.STAGE[dominant]]
+            launches += rep.graph_kernels
+            if rep.status != 0:
+                raise RuntimeError(f"solve reported status {rep.status}")
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # end to end through the public API: pinned host y -> device, solve, x -> pinned host
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty(plan.x_shape, dtype=torch.complex64).pin_memory()
+    prm.timing = 0
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    y_dev = torch.empty_like(y)
+    for k in range(args.steps):
+        flush.zero_()
+        e2e_ev[k][0].record()
+        y_dev.copy_(y_host, non_blocking=True)
+        plan.reconstruct(y_dev, x=x, params=prm, report=False)
+        x_host.copy_(x, non_blocking=True)
+        e2e_ev[k][1].record()
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel class
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    work = stage_work(cfg).get(dominant, {"bytes": None, "flops": None})
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    sm_mhz = clocks.get("sm_mhz") or 1455.0
+    if dominant in ("column", "band", "gram") and work["flops"]:
+        # FP32 ALU bound: 152 SMs x 128 FP32 lanes x 2 flops x the SM clock sampled under load
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = work["flops"] / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms,
+                "peak_note": f"FP32 FMA peak at the sampled median SM clock {sm_mhz:.0f} MHz"}
+    elif work["bytes"]:
+        achieved = work["bytes"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms, "peak_note": peak_src}
+    else:
+        roof = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "kernel": dominant, "launch_ms": per_launch_ms}
+
+    # CPU baseline: the oracle as it stands, on a bounded sample of the same workload
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O  # noqa: F401
+
+        y_np = y.cpu().numpy().astype(np.complex128)
+        t_cpu, sample = oracle_sample(cfg, y_np, g["sens"], reps=5)
+        cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(cfg), "form": "plain FP32 (FP64 reductions)",
+                   "l2": "flushed before every step (512 MB write)", "parallelism": f"replicas x{world}",
+                   "lambda": LAM, "stages_ms_first_warmup": stages_all},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
+                "d2h_bytes_per_step": int(x.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -80,10 +80,28 @@ typedef struct {
   int rank;           /* NULLSPACE rank, 0 < rank < C */
   int warm;           /* 1: x holds the starting point on entry; 0: start from A^H y */
   int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 15 */
-  int reserved[6];
+  int timing;         /* bitmask of (1 << smsm_stage): bracket those launches with CUDA
+                         events inside the solve and report their device time */
+  int reserved[5];
 } smsm_params;
 
 #define SMSM_MAX_OUTER 128
+
+/* Kernel classes of the solve, for smsm_params.timing and smsm_report.stage_ms. */
+typedef enum {
+  SMSM_STAGE_ADJOINT = 0,    /* b = A^H y (row FFT, column stage, row FFT) */
+  SMSM_STAGE_GRAM = 1,       /* Hankel Gram partials + reduction */
+  SMSM_STAGE_EIG = 2,        /* Jacobi sweeps on G */
+  SMSM_STAGE_VAPPLY = 3,     /* eigenvectors from the rotation log */
+  SMSM_STAGE_WEIGHTS = 4,    /* eps schedule + W */
+  SMSM_STAGE_FILTERS = 5,    /* filters from W + image-domain multipliers */
+  SMSM_STAGE_ROWFFT_INV = 6, /* x-direction inverse FFT of the CG vector */
+  SMSM_STAGE_COLUMN = 7,     /* fused column stage of (A^H A + lambda P_W) */
+  SMSM_STAGE_ROWFFT_FWD = 8, /* x-direction forward FFT back to k-space */
+  SMSM_STAGE_BAND = 9,       /* border-band correction of the penalty */
+  SMSM_STAGE_CG = 10,        /* CG vector updates */
+  SMSM_NUM_STAGES = 11
+} smsm_stage;
 
 /* Per-call report, filled after the call's work has finished (host memory). */
 typedef struct {
@@ -94,6 +112,9 @@ typedef struct {
   double rr_end[SMSM_MAX_OUTER];        /* ||r||^2 after its cg_iters steps */
   int sweeps[SMSM_MAX_OUTER];           /* Jacobi sweeps used (max over slices) */
   float elapsed_ms;                     /* device time of the solve (CUDA events) */
+  int graph_kernels;                    /* kernel launches in one solve (nodes of its graph) */
+  float stage_ms[16];                   /* device time per smsm_stage (timed stages only) */
+  int stage_launches[16];               /* timed launches per smsm_stage */
 } smsm_report;
 
 /* Fill *p with the defaults listed above. */

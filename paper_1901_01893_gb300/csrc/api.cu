@@ -97,6 +97,7 @@ static void free_plan(smsm_plan_s* P) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->has_graph) cudaGraphExecDestroy(P->gexec);
+  solver_free_timing(P);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/smsm.h"
 
 // ----------------------------------------------------------------------------
@@ -105,7 +107,9 @@ struct smsm_plan_s {
   cudaStream_t cap_stream;
   smsm_params gparams;
   int has_graph;
+  int graph_kernels;
   cudaEvent_t ev0, ev1;
+  void* tpool;  // TimingPool (solver.cu): events bracketing timed stages
 };
 
 // ----------------------------------------------------------------------------
@@ -133,6 +137,45 @@ void smsm_set_error(const char* fmt, ...);
   } while (0)
 
 // ----------------------------------------------------------------------------
+// stage timing (host)
+// ----------------------------------------------------------------------------
+// Events bracketing the launches of the timed stages (smsm_params.timing).
+// Recorded as external event nodes of the captured graph, so every replay
+// re-records them on the device.
+struct TimingPool {
+  std::vector<cudaEvent_t> ev;  // 2 per bracket
+  std::vector<int> stage;       // stage of bracket k
+  size_t used = 0;              // brackets in the current graph
+};
+
+struct Timer {
+  TimingPool* tp;
+  int mask;
+  cudaStream_t s;
+  cudaError_t err = cudaSuccess;
+  bool on(int stage) const { return tp && ((mask >> stage) & 1); }
+  void begin(int stage) {
+    if (!on(stage) || err != cudaSuccess) return;
+    const size_t k = tp->used;
+    while (tp->ev.size() < 2 * (k + 1)) {
+      cudaEvent_t e;
+      err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return;
+      tp->ev.push_back(e);
+    }
+    if (tp->stage.size() < k + 1) tp->stage.resize(k + 1);
+    tp->stage[k] = stage;
+    err = cudaEventRecordWithFlags(tp->ev[2 * k], s, cudaEventRecordExternal);
+  }
+  void end(int stage) {
+    if (!on(stage) || err != cudaSuccess) return;
+    const size_t k = tp->used;
+    err = cudaEventRecordWithFlags(tp->ev[2 * k + 1], s, cudaEventRecordExternal);
+    tp->used = k + 1;
+  }
+};
+
+// ----------------------------------------------------------------------------
 // launchers implemented in the .cu files (all enqueue on `s`, return status)
 // ----------------------------------------------------------------------------
 // operators.cu
@@ -153,7 +196,7 @@ smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, floa
 smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s);
 // eig.cu
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
-                               cudaStream_t s);
+                               cudaStream_t s, Timer* T);
 smsm_status eig_init_attrs(int Cp);
 size_t eig_jacobi_smem(int Cp);
 smsm_status operators_init_attrs();
@@ -163,5 +206,6 @@ int band_blocks(const smsm_plan_s* P);
 int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
                                smsm_report* report, cudaStream_t s);
+void solver_free_timing(smsm_plan_s* P);
 smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
                              cudaStream_t s);

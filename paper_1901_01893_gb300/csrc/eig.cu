@@ -245,20 +245,26 @@ smsm_status eig_init_attrs(int Cp) {
 size_t eig_jacobi_smem(int Cp) { return jacobi_smem(Cp); }
 
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
-                               cudaStream_t s) {
+                               cudaStream_t s, Timer* T) {
   const int Cp = P->Cp;
   int msw = prm->max_sweeps > 0 ? prm->max_sweeps : 15;
   if (msw > SMSM_MAX_SWEEPS) msw = SMSM_MAX_SWEEPS;
+  if (T) T->begin(SMSM_STAGE_EIG);
   k_jacobi<<<P->L, 1024, jacobi_smem(Cp), s>>>(G, P->eig, P->rotlog, P->sweeps, P->C, Cp, msw, 1e-6f);
   SMSM_LAUNCH_CHECK("k_jacobi");
+  if (T) T->end(SMSM_STAGE_EIG);
+  if (T) T->begin(SMSM_STAGE_VAPPLY);
   dim3 gv(P->L, (P->C + 7) / 8);
   k_vapply<<<gv, 256, (size_t)8 * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, P->C, Cp);
   SMSM_LAUNCH_CHECK("k_vapply");
+  if (T) T->end(SMSM_STAGE_VAPPLY);
+  if (T) T->begin(SMSM_STAGE_WEIGHTS);
   k_eps<<<1, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, P->C, Cp, outer, prm->eps0_rel, prm->eta,
                           prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
   dim3 gw(P->L, (P->C + 15) / 16);
   k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->C, Cp, prm->mode, prm->rank);
   SMSM_LAUNCH_CHECK("k_weights");
+  if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;
 }

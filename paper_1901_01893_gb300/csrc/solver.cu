@@ -10,7 +10,17 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
+
+void solver_free_timing(smsm_plan_s* P) {
+  TimingPool* tp = (TimingPool*)P->tpool;
+  if (!tp) return;
+  for (cudaEvent_t e : tp->ev) cudaEventDestroy(e);
+  delete tp;
+  P->tpool = nullptr;
+}
 
 #define VEC_THREADS 256
 
@@ -147,21 +157,34 @@ __global__ void k_reset_state(SolverState* st) {
 // q = (A^H A + lambda P_W) v.  With with_dots, the per-CTA partials of
 // Re<v, q> go to part_pq_col (column stage, image domain, Parseval) and
 // part_pq_band (border correction).
-smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
-                             cudaStream_t s) {
+static smsm_status normal_pen_timed(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
+                                    cudaStream_t s, Timer* T) {
   const int B = P->L * P->Ns;
   smsm_status st;
+  if (T) T->begin(SMSM_STAGE_ROWFFT_INV);
   if ((st = launch_rowfft_out_T(P, v, P->hA, B, P->N, 1, s))) return st;
+  if (T) T->end(SMSM_STAGE_ROWFFT_INV);
+  if (T) T->begin(SMSM_STAGE_COLUMN);
   if ((st = launch_col(P, COL_NORMAL, 0, P->hA, P->hB, nullptr, lambda != 0.f ? P->multT : nullptr, lambda,
                        with_dots ? P->part_pq_col : nullptr, s)))
     return st;
+  if (T) T->end(SMSM_STAGE_COLUMN);
+  if (T) T->begin(SMSM_STAGE_ROWFFT_FWD);
   if ((st = launch_rowfft_in_T(P, P->hB, q, B, P->N, 0, s))) return st;
+  if (T) T->end(SMSM_STAGE_ROWFFT_FWD);
   if (lambda != 0.f) {
+    if (T) T->begin(SMSM_STAGE_BAND);
     if ((st = launch_band(P, v, q, lambda, with_dots ? P->part_pq_band : nullptr, s))) return st;
+    if (T) T->end(SMSM_STAGE_BAND);
   } else if (with_dots) {
     SMSM_CUDA_TRY(cudaMemsetAsync(P->part_pq_band, 0, sizeof(double) * band_blocks(P), s));
   }
   return SMSM_OK;
+}
+
+smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
+                             cudaStream_t s) {
+  return normal_pen_timed(P, v, q, lambda, with_dots, s, nullptr);
 }
 
 static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s) {
@@ -173,38 +196,55 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
   const float lam = (float)prm->lambda;
   double* rr0 = P->part_rr;
   double* rr1 = P->part_rr + SMSM_PART_MAX;
+  if (prm->timing && !P->tpool) P->tpool = new TimingPool();
+  if (P->tpool) ((TimingPool*)P->tpool)->used = 0;
+  Timer T{(TimingPool*)P->tpool, prm->timing, s};
   k_reset_state<<<1, 1, 0, s>>>(P->st);
   SMSM_LAUNCH_CHECK("k_reset_state");
   // b = A^H y
+  T.begin(SMSM_STAGE_ADJOINT);
   if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, P->Ns * P->Nc, P->M, 1, s))) return st;
   if ((st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s))) return st;
   if ((st = launch_rowfft_in_T(P, P->hB, P->bv, B, P->N, 0, s))) return st;
+  T.end(SMSM_STAGE_ADJOINT);
   if (!prm->warm) SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)B * P->N * P->N,
                                                 cudaMemcpyDeviceToDevice, s));
   for (int k = 0; k < prm->outer_iters; ++k) {
+    T.begin(SMSM_STAGE_GRAM);
     if ((st = launch_gram(P, P->xs, P->G64, s))) return st;
-    if ((st = launch_eig_weights(P, P->G64, k, prm, s))) return st;
+    T.end(SMSM_STAGE_GRAM);
+    if ((st = launch_eig_weights(P, P->G64, k, prm, s, &T))) return st;
+    T.begin(SMSM_STAGE_FILTERS);
     if ((st = launch_filters(P, P->Wf, s))) return st;
-    if ((st = apply_normal_pen(P, P->xs, P->qv, lam, 0, s))) return st;
+    T.end(SMSM_STAGE_FILTERS);
+    if ((st = normal_pen_timed(P, P->xs, P->qv, lam, 0, s, &T))) return st;
+    T.begin(SMSM_STAGE_CG);
     k_cg_init<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv,
                                           (float4*)P->pv, n4, rr0);
     SMSM_LAUNCH_CHECK("k_cg_init");
+    T.end(SMSM_STAGE_CG);
     k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 0, rr0, nvb);
     SMSM_LAUNCH_CHECK("k_record");
     for (int j = 0; j < prm->cg_iters; ++j) {
       double* rin = (j & 1) ? rr1 : rr0;
       double* rout = (j & 1) ? rr0 : rr1;
-      if ((st = apply_normal_pen(P, P->pv, P->qv, lam, 1, s))) return st;
+      if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, &T))) return st;
+      T.begin(SMSM_STAGE_CG);
       k_cg_update<<<nvb, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
                                               (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
                                               lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
       SMSM_LAUNCH_CHECK("k_cg_update");
       k_cg_pupdate<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
       SMSM_LAUNCH_CHECK("k_cg_pupdate");
+      T.end(SMSM_STAGE_CG);
     }
     double* rend = (prm->cg_iters & 1) ? rr1 : rr0;  // bank of the last write
     k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 1, rend, nvb);
     SMSM_LAUNCH_CHECK("k_record");
+  }
+  if (T.err != cudaSuccess) {
+    smsm_set_error("timing events: %s", cudaGetErrorString(T.err));
+    return SMSM_ERR_CUDA;
   }
   return SMSM_OK;
 }
@@ -229,6 +269,16 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
       smsm_set_error("stream capture of the solve failed: %s", cudaGetErrorString(ce));
       return SMSM_ERR_CUDA;
     }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int nk = 0;
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    P->graph_kernels = nk;
     ce = cudaGraphInstantiate(&P->gexec, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
@@ -263,6 +313,16 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
     float ms = 0.f;
     SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
     report->elapsed_ms = ms;
+    report->graph_kernels = P->graph_kernels;
+    TimingPool* tp = (TimingPool*)P->tpool;
+    if (tp && prm->timing) {
+      for (size_t k = 0; k < tp->used; ++k) {
+        float t = 0.f;
+        SMSM_CUDA_TRY(cudaEventElapsedTime(&t, tp->ev[2 * k], tp->ev[2 * k + 1]));
+        report->stage_ms[tp->stage[k]] += t;
+        report->stage_launches[tp->stage[k]] += 1;
+      }
+    }
   }
   return SMSM_OK;
 }

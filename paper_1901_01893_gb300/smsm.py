@@ -19,6 +19,9 @@ SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
 SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_MAX_OUTER = 128
+STAGES = ["adjoint", "gram", "eig", "vapply", "weights", "filters", "rowfft_inv", "column", "rowfft_fwd",
+          "band", "cg"]
+STAGE = {name: k for k, name in enumerate(STAGES)}
 
 
 class Opts(ctypes.Structure):
@@ -29,14 +32,15 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("eps0_rel", ctypes.c_double), ("eta", ctypes.c_double),
                 ("eps_min_rel", ctypes.c_double), ("outer_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("rank", ctypes.c_int), ("warm", ctypes.c_int),
-                ("max_sweeps", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("max_sweeps", ctypes.c_int), ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_done", ctypes.c_int),
                 ("eps", ctypes.c_double * SMSM_MAX_OUTER), ("rr_start", ctypes.c_double * SMSM_MAX_OUTER),
                 ("rr_end", ctypes.c_double * SMSM_MAX_OUTER), ("sweeps", ctypes.c_int * SMSM_MAX_OUTER),
-                ("elapsed_ms", ctypes.c_float)]
+                ("elapsed_ms", ctypes.c_float), ("graph_kernels", ctypes.c_int),
+                ("stage_ms", ctypes.c_float * 16), ("stage_launches", ctypes.c_int * 16)]
 
 
 class SmsmError(RuntimeError):
