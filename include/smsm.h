@@ -194,6 +194,26 @@ smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const sms
 smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, int inverse,
                        void* stream);
 
+/*
+ * The Hankel Gram of smsm_hankel_gram without any device allocation and
+ * without a plan (the paper has no counterpart: this is a service to callers
+ * that may not allocate GPU memory -- a host framework that owns every device
+ * allocation through its own pool, or a real-time path that must not block in
+ * the allocator -- and so cannot call smsm_plan, which allocates).
+ *   x: [mb][shots][n][n] complex64, G: [mb][C][C] complex128, C = shots*filter^2,
+ *   same definition and layouts as smsm_hankel_gram; 1 <= shots <= 8,
+ *   16 <= n <= 512, 1 <= filter <= min(12, n/2).
+ * Scratch: one fixed 8 MiB array compiled into the library (held by every GPU
+ * that loads it until exit).  Geometries needing more than
+ * ceil((n-filter+1)/16) * C^2 * 16 bytes > 8 MiB are rejected with
+ * SMSM_ERR_ARG.  All calls on a device share that array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  Nothing in it needs
+ * clearing between calls.  The first call on a device looks the array's
+ * address up; make it before any stream capture on that device.
+ */
+smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, int n, int filter,
+                                     void* stream);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char* smsm_last_error(void);
 

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
     L.smsm_reconstruct.restype = st
     L.smsm_fft2c.argtypes = [vp, vp, vp, i, i, vp]
     L.smsm_fft2c.restype = st
+    L.smsm_hankel_gram_noalloc.argtypes = [vp, vp, i, i, i, i, vp]
+    L.smsm_hankel_gram_noalloc.restype = st
     L.smsm_last_error.argtypes = []
     L.smsm_last_error.restype = ctypes.c_char_p
     L.smsm_default_params.argtypes = [ctypes.POINTER(Params)]
@@ -100,6 +102,18 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
     return p
+
+
+def smsm_hankel_gram_noalloc(x: torch.Tensor, filter: int, G: torch.Tensor | None = None) -> torch.Tensor:
+    """Hankel Gram of x [mb][shots][n][n] without a plan and without any device
+    allocation inside the library (G is allocated here by torch when not given)."""
+    mb, shots, n, _ = x.shape
+    C = shots * filter * filter
+    if G is None:
+        G = torch.empty((mb, C, C), dtype=torch.complex128, device=x.device)
+    _check(lib().smsm_hankel_gram_noalloc(_dev(x, x.shape, "x"), _dev(G, (mb, C, C), "G", torch.complex128),
+                                          mb, shots, n, filter, _stream()))
+    return G
 
 
 def _stream() -> ctypes.c_void_p:
