@@ -53,11 +53,25 @@ typedef enum {
 
 typedef enum { SMSM_MODE_IRLS = 0, SMSM_MODE_NULLSPACE = 1 } smsm_mode;
 
-/* Plan options (all zero = defaults). */
+/*
+ * Plan options (all zero = defaults).
+ * batch = D > 1 makes the plan solve D independent problems at once -- e.g.
+ * the diffusion directions of one slice group, which share the geometry and
+ * the coil maps.  Every per-problem array then gains a leading [D] dimension
+ * (x: [D][L][Ns][N][N], y: [D][Ns][Nc][N/Ns][N], phase: [D][L][Ns][N][N],
+ * G and W: [D][L][C][C]); coil maps stay [L][Nc][N][N].  Each problem keeps
+ * its own CG scalars and eps schedule.
+ */
 typedef struct {
   int caipi_div;   /* CAIPI FOV shift is FOV/caipi_div per slice index; 0 -> mb (Eq. 1) */
-  int reserved[7];
+  int batch;       /* D, number of problems per call; 0 -> 1 (at most 4096) */
+  int flags;       /* SMSM_FLAG_* bits */
+  int reserved[5];
 } smsm_opts;
+
+/* smsm_opts.flags: use the shape-generic kernels even where a specialised fast
+ * path exists (same results up to rounding; for testing and comparison). */
+#define SMSM_FLAG_GENERIC_KERNELS 1
 
 /*
  * Solver parameters.  The paper minimises Eq. 10 with an augmented-Lagrangian
@@ -103,7 +117,9 @@ typedef enum {
   SMSM_NUM_STAGES = 11
 } smsm_stage;
 
-/* Per-call report, filled after the call's work has finished (host memory). */
+/* Per-call report, filled after the call's work has finished (host memory).
+ * With batch > 1, status is the first nonzero status over the problems and the
+ * per-iteration arrays follow problem 0. */
 typedef struct {
   int status;                           /* smsm_status of the device-side checks */
   int outer_done;                       /* outer iterations run */

@@ -58,6 +58,8 @@ static bool factor_radix(int n, FftDesc* d) {
     d->rad[d->np++] = 3;
     m /= 3;
   }
+  d->code = 0;
+  for (int p = 0; p < d->np; ++p) d->code |= (unsigned)(d->rad[p] == 4 ? 2 : (d->rad[p] == 3 ? 1 : 0)) << (2 * p);
   return m == 1 && n >= 2;
 }
 
@@ -139,6 +141,11 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     return SMSM_ERR_ARG;
   }
   const int caipi_div = (opts && opts->caipi_div > 0) ? opts->caipi_div : mb;
+  const int D = (opts && opts->batch > 0) ? opts->batch : 1;
+  if (D > 4096) {
+    smsm_set_error("smsm_plan: batch must be in [1, 4096] (got %d)", D);
+    return SMSM_ERR_ARG;
+  }
 
   smsm_plan_s* P = (smsm_plan_s*)calloc(1, sizeof(smsm_plan_s));
   if (!P) {
@@ -154,6 +161,9 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   P->Cp = Cp;
   P->M = M;
   P->Ldiv = caipi_div;
+  P->D = D;
+  P->LD = D * mb;
+  P->flags = opts ? opts->flags : 0;
   P->P1 = N - r + 1;
   P->R2 = 2 * r - 1;
   P->fN = fN;
@@ -166,7 +176,9 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
 
   smsm_status st = SMSM_OK;
   const size_t NN = (size_t)N * N;
-  const size_t nvec = (size_t)mb * shots * NN;
+  const size_t nvec = (size_t)D * mb * shots * NN;  // one batch of unknowns
+  const size_t LD = (size_t)D * mb;
+  const size_t nyv = (size_t)D * shots * coils * M * N;
   const int R2 = P->R2;
 #define A(ptr, cnt) \
   if (!st) st = dalloc(P, &P->ptr, (size_t)(cnt))
@@ -178,28 +190,28 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(sensT, (size_t)mb * coils * NN);
   A(hA, nvec);
   A(hB, nvec);
-  A(yh, (size_t)shots * coils * M * N);
+  A(yh, nyv);
   A(phaseT, nvec);
   A(xs, nvec);
   A(bv, nvec);
   A(rv, nvec);
   A(pv, nvec);
   A(qv, nvec);
-  A(ybuf, (size_t)shots * coils * M * N);
-  A(G64, (size_t)mb * C * C);
-  A(Gpart, (size_t)mb * P->gram_nkx * C * C);
-  A(eig, (size_t)mb * Cp);
-  A(rotlog, (size_t)mb * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2));
-  A(sweeps, mb);
-  A(V, (size_t)mb * C * C);
-  A(Wf, (size_t)mb * C * C);
-  A(wper, (size_t)mb * shots * shots * R2 * R2);
-  A(wcls, (size_t)mb * R2 * R2 * shots * shots * R2 * R2);
-  A(multT, (size_t)mb * shots * shots * NN);
-  A(part_pq_col, SMSM_PART_MAX);
-  A(part_pq_band, SMSM_PART_MAX);
-  A(part_rr, 2 * SMSM_PART_MAX);
-  A(st, 1);
+  A(ybuf, nyv);
+  A(G64, LD * C * C);
+  A(Gpart, LD * P->gram_nkx * C * C);
+  A(eig, LD * Cp);
+  A(rotlog, LD * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2));
+  A(sweeps, LD);
+  A(V, LD * C * C);
+  A(Wf, LD * C * C);
+  A(wper, LD * shots * shots * R2 * R2);
+  A(wcls, LD * R2 * R2 * shots * shots * R2 * R2);
+  A(multT, LD * shots * shots * NN);
+  A(part_pq_col, (size_t)D * SMSM_PART_MAX);
+  A(part_pq_band, (size_t)D * SMSM_PART_MAX);
+  A(part_rr, (size_t)2 * D * SMSM_PART_MAX);
+  A(st, D);
   A(rep, 1);
 #undef A
   if (st) {
@@ -253,6 +265,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     st = upload(P->Etab, h);
   }
   if (!st) st = operators_init_attrs();
+  if (!st) st = colfast_init_attrs();
   if (!st) st = eig_init_attrs(Cp);
   if (!st && smsm_col_smem_bytes(P) > 200 * 1024) {
     smsm_set_error("smsm_plan: column stage would need %zu bytes of shared memory", smsm_col_smem_bytes(P));
@@ -262,7 +275,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     cudaError_t e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&P->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&P->ev1);
-    if (e == cudaSuccess) e = cudaMemset(P->part_pq_band, 0, sizeof(double) * SMSM_PART_MAX);
+    if (e == cudaSuccess) e = cudaMemset(P->part_pq_band, 0, sizeof(double) * SMSM_PART_MAX * D);
     if (e != cudaSuccess) {
       smsm_set_error("smsm_plan: %s", cudaGetErrorString(e));
       st = SMSM_ERR_CUDA;
@@ -342,13 +355,13 @@ extern "C" smsm_status smsm_forward(smsm_plan_t plan, const void* x, const void*
   if (phase) CHECK_PTR("smsm_forward", phase);
   smsm_status st;
   if ((st = need_sens(plan, "smsm_forward"))) return st;
-  const int L = plan->L, Ns = plan->Ns, N = plan->N;
+  const int L = plan->L, Ns = plan->Ns, N = plan->N, D = plan->D;
   cudaStream_t s = S(stream);
-  if (phase && (st = launch_transpose((const float2*)phase, plan->phaseT, L * Ns, N, N, s))) return st;
-  if ((st = launch_rowfft_out_T(plan, (const float2*)x, plan->hA, phase ? L : L * Ns, N, 1, s))) return st;
+  if (phase && (st = launch_transpose((const float2*)phase, plan->phaseT, D * L * Ns, N, N, s))) return st;
+  if ((st = launch_rowfft_out_T(plan, (const float2*)x, plan->hA, D * (phase ? L : L * Ns), N, 1, s))) return st;
   if ((st = launch_col(plan, COL_FWD, phase != nullptr, plan->hA, plan->yh, plan->phaseT, nullptr, 0.f, nullptr, s)))
     return st;
-  return launch_rowfft_in_T(plan, plan->yh, (float2*)y, Ns * plan->Nc, plan->M, 0, s);
+  return launch_rowfft_in_T(plan, plan->yh, (float2*)y, D * Ns * plan->Nc, plan->M, 0, s);
 }
 
 extern "C" smsm_status smsm_adjoint(smsm_plan_t plan, const void* y, const void* phase, void* x, void* stream) {
@@ -358,13 +371,13 @@ extern "C" smsm_status smsm_adjoint(smsm_plan_t plan, const void* y, const void*
   if (phase) CHECK_PTR("smsm_adjoint", phase);
   smsm_status st;
   if ((st = need_sens(plan, "smsm_adjoint"))) return st;
-  const int L = plan->L, Ns = plan->Ns, N = plan->N;
+  const int L = plan->L, Ns = plan->Ns, N = plan->N, D = plan->D;
   cudaStream_t s = S(stream);
-  if ((st = launch_rowfft_out_T(plan, (const float2*)y, plan->yh, Ns * plan->Nc, plan->M, 1, s))) return st;
-  if (phase && (st = launch_transpose((const float2*)phase, plan->phaseT, L * Ns, N, N, s))) return st;
+  if ((st = launch_rowfft_out_T(plan, (const float2*)y, plan->yh, D * Ns * plan->Nc, plan->M, 1, s))) return st;
+  if (phase && (st = launch_transpose((const float2*)phase, plan->phaseT, D * L * Ns, N, N, s))) return st;
   if ((st = launch_col(plan, COL_ADJ, phase != nullptr, plan->yh, plan->hB, plan->phaseT, nullptr, 0.f, nullptr, s)))
     return st;
-  return launch_rowfft_in_T(plan, plan->hB, (float2*)x, phase ? L : L * Ns, N, 0, s);
+  return launch_rowfft_in_T(plan, plan->hB, (float2*)x, D * (phase ? L : L * Ns), N, 0, s);
 }
 
 extern "C" smsm_status smsm_hankel_gram(smsm_plan_t plan, const void* x, void* G, void* stream) {
@@ -385,7 +398,7 @@ extern "C" smsm_status smsm_apply_filters(smsm_plan_t plan, const void* W, const
   }
   cudaStream_t s = S(stream);
   smsm_status st;
-  const int B = plan->L * plan->Ns;
+  const int B = plan->D * plan->L * plan->Ns;
   if ((st = launch_w_from_c128(plan, (const double2*)W, plan->Wf, s))) return st;
   if ((st = launch_filters(plan, plan->Wf, s))) return st;
   if ((st = launch_rowfft_out_T(plan, (const float2*)x, plan->hA, B, plan->N, 1, s))) return st;
@@ -403,7 +416,7 @@ extern "C" smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, i
     return SMSM_ERR_ARG;
   }
   cudaStream_t s = S(stream);
-  const int chunk = plan->L * plan->Ns;
+  const int chunk = plan->D * plan->L * plan->Ns;
   const size_t NN = (size_t)plan->N * plan->N;
   smsm_status st;
   for (int b0 = 0; b0 < count; b0 += chunk) {

@@ -44,6 +44,7 @@ __device__ __forceinline__ void cfmacj(float2& acc, float2 a, float2 b) {
 struct FftDesc {
   int n;
   int np;
+  unsigned code;  // radix of pass p in bits [2p, 2p+2): 0 -> 2, 1 -> 3, 2 -> 4 (no indexed param access)
   int rad[12];
 };
 
@@ -73,6 +74,9 @@ struct DevReport {
 
 struct smsm_plan_s {
   int L, Ns, Nc, N, r, C, Cp /* C rounded up to even */, M, Ldiv, P1 /* N-r+1 */, R2 /* 2r-1 */;
+  int D;   // batch: independent problems (diffusion directions) sharing geometry and coil maps
+  int flags;  // smsm_opts.flags
+  int LD;  // D * L: number of (direction, slice) Hankel matrices
   int nband;  // pixels within r-1 of an edge
   int dev;
   FftDesc fN, fM;
@@ -98,8 +102,8 @@ struct smsm_plan_s {
   float2* wper;      // [L][Ns][Ns][R2*R2]
   float2* wcls;      // [L][R2*R2][Ns][Ns][R2*R2]
   float2* multT;     // [L][Ns][Ns][N(x)][N(y)]
-  double *part_pq_col, *part_pq_band, *part_rr;  // partial sums; part_rr has 2 banks
-  SolverState* st;
+  double *part_pq_col, *part_pq_band, *part_rr;  // partial sums [D][PART]; part_rr: [2 banks][D][PART]
+  SolverState* st;   // [D]
   DevReport* rep;
   size_t bytes;
   // graph cache for smsm_reconstruct
@@ -185,6 +189,28 @@ smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* 
 smsm_status launch_rowfft_in_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
                                int inverse, cudaStream_t s);
 enum ColMode { COL_FWD = 0, COL_ADJ = 1, COL_NORMAL = 2, COL_PEN = 3 };
+// Column-stage arguments (operators.cu, colfast.cu)
+struct ColArgs {
+  const float2* in;  // (offset per direction inside the kernel)
+  float2* out;
+  const float2* sensT;   // [L][Nc][x][y]
+  const float2* phaseT;  // [L][Ns][x][y]
+  const float2* multT;   // [L][Ns][Ns][x][y]
+  const float2* twN;
+  const float2* twM;
+  const float2* tw_shot;  // [Ns][N]
+  const float2* cph;      // [L][Ns][M]
+  FftDesc fN, fM;
+  int L, Ns, Nc, N, M;
+  float sN, lambda;
+  double* dot_part;  // [N] per-CTA partial of Re<img, acc> (nullable)
+};
+
+// colfast.cu: warp-shuffle column stage of (A^H A + lambda P_W); returns SMSM_ERR_ARG when the
+// geometry has no fast path (the caller then uses the generic kernel)
+smsm_status launch_col_fast(const smsm_plan_s* P, const ColArgs& a, cudaStream_t s);
+smsm_status colfast_init_attrs();
+
 smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const float2* in, float2* out,
                        const float2* phaseT, const float2* multT, float lambda, double* dot_part,
                        cudaStream_t s);

@@ -156,14 +156,16 @@ __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog,
   for (int j = lane; j < C; j += 32) Vr[j] = row[j];
 }
 
-// eps schedule and report (one CTA): eps_1 = eps0_rel * max eigenvalue, then eps_k = max(eps_{k-1}/eta, eps_min)
+// eps schedule and report, one CTA per direction d: eps_1 = eps0_rel * (largest
+// eigenvalue over d's slices), then eps_k = max(eps_{k-1}/eta, eps_min).
 __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ sweeps, SolverState* st, DevReport* rep,
                       int L, int C, int Cp, int outer, double eps0_rel, double eta, double eps_min_rel) {
   __shared__ float mx[256];
+  const int d = blockIdx.x;
   float m = 0.f;
   for (int e = threadIdx.x; e < L * C; e += blockDim.x) {
     int l = e / C, j = e - l * C;
-    m = fmaxf(m, eig[(size_t)l * Cp + j]);
+    m = fmaxf(m, eig[(size_t)(d * L + l) * Cp + j]);
   }
   mx[threadIdx.x] = m;
   __syncthreads();
@@ -172,17 +174,18 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    SolverState* sd = st + d;
     if (outer == 0) {
-      st->eps0 = eps0_rel * (double)mx[0];
-      st->eps = st->eps0;
-      st->eps_min = eps_min_rel * st->eps0;
+      sd->eps0 = eps0_rel * (double)mx[0];
+      sd->eps = sd->eps0;
+      sd->eps_min = eps_min_rel * sd->eps0;
     } else {
-      st->eps = fmax(st->eps / eta, st->eps_min);
+      sd->eps = fmax(sd->eps / eta, sd->eps_min);
     }
-    int smax = 0;
-    for (int l = 0; l < L; ++l) smax = max(smax, sweeps[l]);
-    if (outer < SMSM_MAX_OUTER) {
-      rep->eps[outer] = st->eps;
+    if (d == 0 && outer < SMSM_MAX_OUTER) {  // the report follows direction 0
+      int smax = 0;
+      for (int l = 0; l < L; ++l) smax = max(smax, sweeps[l]);
+      rep->eps[outer] = sd->eps;
       rep->sweeps[outer] = smax;
     }
   }
@@ -191,12 +194,12 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
 // W[a][b] = sum_j V[a][j] f_j conj(V[b][j])
 __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, const float* __restrict__ eig,
                                                  const SolverState* __restrict__ st, float2* __restrict__ W, int C,
-                                                 int Cp, int mode, int rank) {
+                                                 int Cp, int mode, int rank, int L) {
   __shared__ float f[SMSM_MAX_C];
   __shared__ float2 Va[16][SMSM_MAX_C];
   const int l = blockIdx.x, a0 = blockIdx.y * 16;
   const float* s = eig + (size_t)l * Cp;
-  const double eps = st->eps;
+  const double eps = st[l / L].eps;  // l is the flat (direction, slice) index
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     if (mode == SMSM_MODE_NULLSPACE) {
       int rk = 0;
@@ -250,20 +253,20 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   int msw = prm->max_sweeps > 0 ? prm->max_sweeps : 15;
   if (msw > SMSM_MAX_SWEEPS) msw = SMSM_MAX_SWEEPS;
   if (T) T->begin(SMSM_STAGE_EIG);
-  k_jacobi<<<P->L, 1024, jacobi_smem(Cp), s>>>(G, P->eig, P->rotlog, P->sweeps, P->C, Cp, msw, 1e-6f);
+  k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, P->eig, P->rotlog, P->sweeps, P->C, Cp, msw, 1e-6f);
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  dim3 gv(P->L, (P->C + 7) / 8);
+  dim3 gv(P->LD, (P->C + 7) / 8);
   k_vapply<<<gv, 256, (size_t)8 * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, P->C, Cp);
   SMSM_LAUNCH_CHECK("k_vapply");
   if (T) T->end(SMSM_STAGE_VAPPLY);
   if (T) T->begin(SMSM_STAGE_WEIGHTS);
-  k_eps<<<1, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, P->C, Cp, outer, prm->eps0_rel, prm->eta,
+  k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, P->C, Cp, outer, prm->eps0_rel, prm->eta,
                           prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
-  dim3 gw(P->L, (P->C + 15) / 16);
-  k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->C, Cp, prm->mode, prm->rank);
+  dim3 gw(P->LD, (P->C + 15) / 16);
+  k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->C, Cp, prm->mode, prm->rank, P->L);
   SMSM_LAUNCH_CHECK("k_weights");
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;

@@ -60,7 +60,8 @@ __device__ float2* fft_smem(float2* a, float2* b, int nbatch, int bstride, const
   float2* src = a;
   float2* dst = b;
   for (int ps = 0; ps < d.np; ++ps) {
-    const int R = d.rad[ps];
+    const unsigned rc = (d.code >> (2 * ps)) & 3u;
+    const int R = rc == 2u ? 4 : (rc == 1u ? 3 : 2);
     const int nR = n / R;
     const int tstep = n / (s * R);
     const int ntask = nbatch * nR;

@@ -133,10 +133,10 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
   const int nkx = P->gram_nkx;
   const int TW = GCH + P->r - 1;
   size_t sm = (size_t)P->Ns * TW * TW * sizeof(float2);
-  dim3 grid(nkx, ntile, P->L);
+  dim3 grid(nkx, ntile, P->LD);
   k_gram_part<<<grid, 256, sm, s>>>(x, P->Gpart, P->Ns, P->N, P->r, P->C, P->P1, nkx, tside);
   SMSM_LAUNCH_CHECK("k_gram_part");
-  k_gram_reduce<<<256, 256, 0, s>>>(P->Gpart, G, P->L, P->C, nkx);
+  k_gram_reduce<<<256, 256, 0, s>>>(P->Gpart, G, P->LD, P->C, nkx);
   SMSM_LAUNCH_CHECK("k_gram_reduce");
   return SMSM_OK;
 }
@@ -217,17 +217,17 @@ __global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict
 }
 
 smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s) {
-  k_c128_to_c64<<<128, 256, 0, s>>>(W64, W, (size_t)P->L * P->C * P->C);
+  k_c128_to_c64<<<128, 256, 0, s>>>(W64, W, (size_t)P->LD * P->C * P->C);
   SMSM_LAUNCH_CHECK("k_c128_to_c64");
   return SMSM_OK;
 }
 
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s) {
   const int R2 = P->R2;
-  dim3 g1(R2 * R2 + 1, P->Ns * P->Ns, P->L);
+  dim3 g1(R2 * R2 + 1, P->Ns * P->Ns, P->LD);
   k_filters<<<g1, 128, 0, s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C);
   SMSM_LAUNCH_CHECK("k_filters");
-  dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->L);
+  dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->LD);
   k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
   SMSM_LAUNCH_CHECK("k_mult");
   return SMSM_OK;
@@ -264,13 +264,13 @@ __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, floa
                                               double* __restrict__ dot_part) {
   __shared__ double red[256];
   const int R2 = 2 * r - 1;
-  const int total = L * nband * Ns;
+  const int total = L * nband * Ns;  // per direction
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   double dsum = 0.0;
   if (idx < total) {
     const int i = idx % Ns;
     const int t = idx / Ns;
-    const int bp = t % nband, l = t / nband;
+    const int bp = t % nband, l = blockIdx.y * L + t / nband;  // flat (direction, slice)
     int ny, nx;
     band_pixel(bp, N, r, ny, nx);
     const int cls = pix_class(ny, N, r) * R2 + pix_class(nx, N, r);
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, floa
       if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
       __syncthreads();
     }
-    if (threadIdx.x == 0) dot_part[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) dot_part[(size_t)blockIdx.y * SMSM_PART_MAX + blockIdx.x] = red[0];
   }
 }
 
@@ -322,7 +322,8 @@ smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, floa
                         cudaStream_t s) {
   const int nb = band_blocks(P);
   if (nb <= 0) return SMSM_OK;
-  k_band<<<nb, 256, 0, s>>>(x, out, P->wper, P->wcls, P->L, P->Ns, P->N, P->r, P->nband, scale, dot_part);
+  k_band<<<dim3(nb, P->D), 256, 0, s>>>(x, out, P->wper, P->wcls, P->L, P->Ns, P->N, P->r, P->nband, scale,
+                                        dot_part);
   SMSM_LAUNCH_CHECK("k_band");
   return SMSM_OK;
 }

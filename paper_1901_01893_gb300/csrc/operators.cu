@@ -143,22 +143,6 @@ smsm_status launch_rowfft_in_T(const smsm_plan_s* P, const float2* in, float2* o
 // ---------------------------------------------------------------------------
 // Column stage: one CTA per image column x.
 // ---------------------------------------------------------------------------
-struct ColArgs {
-  const float2* in;
-  float2* out;
-  const float2* sensT;   // [L][Nc][x][y]
-  const float2* phaseT;  // [L][Ns][x][y]
-  const float2* multT;   // [L][Ns][Ns][x][y]
-  const float2* twN;
-  const float2* twM;
-  const float2* tw_shot;  // [Ns][N]
-  const float2* cph;      // [L][Ns][M]
-  FftDesc fN, fM;
-  int L, Ns, Nc, N, M;
-  float sN, lambda;
-  double* dot_part;  // [N] per-CTA partial of Re<img, acc> (nullable)
-};
-
 #define COL_THREADS 256
 #define SMSM_MAX_NS 8
 
@@ -176,7 +160,8 @@ __device__ double block_sum_double(double v, double* red) {
 }
 
 template <int MODE, bool PHASE>
-__global__ void __launch_bounds__(COL_THREADS) k_col(ColArgs a) {
+__global__ void __launch_bounds__(COL_THREADS) k_col(const ColArgs a_param) {
+  ColArgs a = a_param;  // per-direction offsets are applied to this copy
   extern __shared__ float2 sm[];
   __shared__ double red[COL_THREADS];
   const int L = a.L, Ns = a.Ns, N = a.N, M = a.M, Nc = a.Nc;
@@ -192,6 +177,22 @@ __global__ void __launch_bounds__(COL_THREADS) k_col(ColArgs a) {
   const int x = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t NN = (size_t)N * N;
+  // batch: direction d has its own input, output, phase, multipliers and partials
+  {
+    const size_t d = blockIdx.y;
+    const size_t ydir = (size_t)Ns * Nc * N * M;
+    if (MODE == COL_ADJ)
+      a.in += d * ydir;
+    else
+      a.in += d * (size_t)(PHASE ? L : B) * NN;
+    if (MODE == COL_FWD)
+      a.out += d * ydir;
+    else
+      a.out += d * (size_t)((MODE == COL_ADJ && PHASE) ? L : B) * NN;
+    if (a.phaseT) a.phaseT += d * (size_t)B * NN;
+    if (a.multT) a.multT += d * (size_t)B * Ns * NN;
+    if (a.dot_part) a.dot_part += d * SMSM_PART_MAX;
+  }
 
   for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
   for (int e = tid; e < M; e += nt) sTwM[e] = a.twM[e];
@@ -350,8 +351,8 @@ static size_t col_smem(const smsm_plan_s* P) {
 }
 
 template <int MODE, bool PH>
-static smsm_status launch_col_t(const ColArgs& a, int N, size_t sm, cudaStream_t s) {
-  k_col<MODE, PH><<<N, COL_THREADS, sm, s>>>(a);
+static smsm_status launch_col_t(const ColArgs& a, int N, int D, size_t sm, cudaStream_t s) {
+  k_col<MODE, PH><<<dim3(N, D), COL_THREADS, sm, s>>>(a);
   SMSM_LAUNCH_CHECK("k_col");
   return SMSM_OK;
 }
@@ -379,6 +380,10 @@ smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const flo
   a.sN = P->sN;
   a.lambda = lambda;
   a.dot_part = dot_part;
+  if (mode == COL_NORMAL && !with_phase && !(P->flags & SMSM_FLAG_GENERIC_KERNELS)) {
+    smsm_status fst = launch_col_fast(P, a, s);
+    if (fst != SMSM_ERR_ARG) return fst;  // SMSM_ERR_ARG: no fast path for this geometry
+  }
   size_t sm = col_smem(P);
   if (sm > 200 * 1024) {
     smsm_set_error("column stage needs %zu bytes of shared memory (> 200 KB)", sm);
@@ -386,13 +391,13 @@ smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const flo
   }
   switch (mode) {
     case COL_FWD:
-      return with_phase ? launch_col_t<COL_FWD, true>(a, P->N, sm, s) : launch_col_t<COL_FWD, false>(a, P->N, sm, s);
+      return with_phase ? launch_col_t<COL_FWD, true>(a, P->N, P->D, sm, s) : launch_col_t<COL_FWD, false>(a, P->N, P->D, sm, s);
     case COL_ADJ:
-      return with_phase ? launch_col_t<COL_ADJ, true>(a, P->N, sm, s) : launch_col_t<COL_ADJ, false>(a, P->N, sm, s);
+      return with_phase ? launch_col_t<COL_ADJ, true>(a, P->N, P->D, sm, s) : launch_col_t<COL_ADJ, false>(a, P->N, P->D, sm, s);
     case COL_NORMAL:
-      return launch_col_t<COL_NORMAL, false>(a, P->N, sm, s);
+      return launch_col_t<COL_NORMAL, false>(a, P->N, P->D, sm, s);
     default:
-      return launch_col_t<COL_PEN, false>(a, P->N, sm, s);
+      return launch_col_t<COL_PEN, false>(a, P->N, P->D, sm, s);
   }
 }
 

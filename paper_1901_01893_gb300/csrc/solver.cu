@@ -24,10 +24,13 @@ void solver_free_timing(smsm_plan_s* P) {
 
 #define VEC_THREADS 256
 
+// CTAs per direction of the CG vector kernels
 int vec_blocks(const smsm_plan_s* P) {
   const size_t n2 = (size_t)P->L * P->Ns * P->N * P->N / 2;  // float4 = two complex
   size_t b = (n2 + VEC_THREADS - 1) / VEC_THREADS;
-  if (b > 4 * 152) b = 4 * 152;
+  size_t cap = (size_t)(4 * 152 + P->D - 1) / P->D;
+  if (cap < 8) cap = 8;
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -62,11 +65,23 @@ __device__ __forceinline__ double norm2_4(float4 v) {
   return (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
 }
 
+// Vectors are [D][n4] float4 (direction d = blockIdx.y); partial arrays are
+// [D][SMSM_PART_MAX]; every direction has its own CG scalars.
+#define DIR_OFFSETS(n4)                          \
+  const size_t d_ = blockIdx.y;                 \
+  const size_t off_ = d_ * (n4);                \
+  const size_t poff_ = d_ * SMSM_PART_MAX;
+
 // r = b - q; p = r; partial ||r||^2
 __global__ void __launch_bounds__(VEC_THREADS) k_cg_init(const float4* __restrict__ b, const float4* __restrict__ q,
                                                          float4* __restrict__ r, float4* __restrict__ p, size_t n4,
                                                          double* __restrict__ part_rr) {
   __shared__ double red[VEC_THREADS];
+  DIR_OFFSETS(n4)
+  b += off_;
+  q += off_;
+  r += off_;
+  p += off_;
   double s = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
     float4 bv = b[e], qv = q[e];
@@ -75,7 +90,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_init(const float4* __restric
     p[e] = rv;
     s += norm2_4(rv);
   }
-  block_partial(s, red, part_rr);
+  block_partial(s, red, part_rr + poff_);
 }
 
 // alpha = <r,r>/<p,q>; x += alpha p; r -= alpha q; partial ||r||^2
@@ -86,12 +101,17 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ 
                                                            const double* __restrict__ rr_in, int nrr,
                                                            double* __restrict__ rr_out, SolverState* st) {
   __shared__ double red[VEC_THREADS];
-  const double pq = sum_parts(pq_col, ncol, pq_band, nband, red);
-  const double rr = sum_parts(rr_in, nrr, nullptr, 0, red);
+  DIR_OFFSETS(n4)
+  x += off_;
+  r += off_;
+  p += off_;
+  q += off_;
+  const double pq = sum_parts(pq_col + poff_, ncol, pq_band + poff_, nband, red);
+  const double rr = sum_parts(rr_in + poff_, nrr, nullptr, 0, red);
   double alpha = rr / pq;
   if (!(pq > 0.0) || !isfinite(alpha)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st->status == 0)
-      st->status = isfinite(pq) ? SMSM_ERR_NOT_PD : SMSM_ERR_DIVERGED;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st[d_].status == 0)
+      st[d_].status = isfinite(pq) ? SMSM_ERR_NOT_PD : SMSM_ERR_DIVERGED;
     alpha = 0.0;
   }
   const float a = (float)alpha;
@@ -111,7 +131,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ 
     r[e] = rv;
     s += norm2_4(rv);
   }
-  block_partial(s, red, rr_out);
+  block_partial(s, red, rr_out + poff_);
 }
 
 // beta = rr_new/rr_old; p = r + beta p
@@ -119,8 +139,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_pupdate(const float4* __rest
                                                             size_t n4, const double* __restrict__ rr_new,
                                                             const double* __restrict__ rr_old, int nrr) {
   __shared__ double red[VEC_THREADS];
-  const double rn = sum_parts(rr_new, nrr, nullptr, 0, red);
-  const double ro = sum_parts(rr_old, nrr, nullptr, 0, red);
+  DIR_OFFSETS(n4)
+  r += off_;
+  p += off_;
+  const double rn = sum_parts(rr_new + poff_, nrr, nullptr, 0, red);
+  const double ro = sum_parts(rr_old + poff_, nrr, nullptr, 0, red);
   double beta = ro > 0.0 ? rn / ro : 0.0;
   if (!isfinite(beta)) beta = 0.0;
   const float bta = (float)beta;
@@ -135,7 +158,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_pupdate(const float4* __rest
   }
 }
 
-// which = 0: record ||r||^2 at the start of outer iteration `outer`; 1: at its end
+// which = 0: record ||r||^2 of direction 0 at the start of outer iteration `outer`; 1: at its end
 __global__ void k_record(DevReport* rep, int outer, int which, const double* __restrict__ rr, int nrr) {
   __shared__ double red[VEC_THREADS];
   const double a = sum_parts(rr, nrr, nullptr, 0, red);
@@ -147,11 +170,13 @@ __global__ void k_record(DevReport* rep, int outer, int which, const double* __r
   }
 }
 
-__global__ void k_reset_state(SolverState* st) {
-  st->status = 0;
-  st->eps = 0.0;
-  st->eps0 = 0.0;
-  st->eps_min = 0.0;
+__global__ void k_reset_state(SolverState* st, int D) {
+  for (int d = threadIdx.x; d < D; d += blockDim.x) {
+    st[d].status = 0;
+    st[d].eps = 0.0;
+    st[d].eps0 = 0.0;
+    st[d].eps_min = 0.0;
+  }
 }
 
 // q = (A^H A + lambda P_W) v.  With with_dots, the per-CTA partials of
@@ -162,7 +187,7 @@ static smsm_status normal_pen_timed(smsm_plan_s* P, const float2* v, float2* q, 
   const int B = P->L * P->Ns;
   smsm_status st;
   if (T) T->begin(SMSM_STAGE_ROWFFT_INV);
-  if ((st = launch_rowfft_out_T(P, v, P->hA, B, P->N, 1, s))) return st;
+  if ((st = launch_rowfft_out_T(P, v, P->hA, P->D * B, P->N, 1, s))) return st;
   if (T) T->end(SMSM_STAGE_ROWFFT_INV);
   if (T) T->begin(SMSM_STAGE_COLUMN);
   if ((st = launch_col(P, COL_NORMAL, 0, P->hA, P->hB, nullptr, lambda != 0.f ? P->multT : nullptr, lambda,
@@ -170,14 +195,14 @@ static smsm_status normal_pen_timed(smsm_plan_s* P, const float2* v, float2* q, 
     return st;
   if (T) T->end(SMSM_STAGE_COLUMN);
   if (T) T->begin(SMSM_STAGE_ROWFFT_FWD);
-  if ((st = launch_rowfft_in_T(P, P->hB, q, B, P->N, 0, s))) return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, q, P->D * B, P->N, 0, s))) return st;
   if (T) T->end(SMSM_STAGE_ROWFFT_FWD);
   if (lambda != 0.f) {
     if (T) T->begin(SMSM_STAGE_BAND);
     if ((st = launch_band(P, v, q, lambda, with_dots ? P->part_pq_band : nullptr, s))) return st;
     if (T) T->end(SMSM_STAGE_BAND);
   } else if (with_dots) {
-    SMSM_CUDA_TRY(cudaMemsetAsync(P->part_pq_band, 0, sizeof(double) * band_blocks(P), s));
+    SMSM_CUDA_TRY(cudaMemsetAsync(P->part_pq_band, 0, sizeof(double) * SMSM_PART_MAX * P->D, s));
   }
   return SMSM_OK;
 }
@@ -190,25 +215,28 @@ smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float l
 static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s) {
   smsm_status st;
   const int B = P->L * P->Ns;
-  const size_t n4 = (size_t)B * P->N * P->N / 2;
+  const int D = P->D;
+  const size_t n4 = (size_t)B * P->N * P->N / 2;  // float4 per direction
   const int nvb = vec_blocks(P);
   const int nbb = band_blocks(P);
   const float lam = (float)prm->lambda;
   double* rr0 = P->part_rr;
-  double* rr1 = P->part_rr + SMSM_PART_MAX;
+  double* rr1 = P->part_rr + (size_t)SMSM_PART_MAX * D;
+  const dim3 vg(nvb, D);
   if (prm->timing && !P->tpool) P->tpool = new TimingPool();
   if (P->tpool) ((TimingPool*)P->tpool)->used = 0;
   Timer T{(TimingPool*)P->tpool, prm->timing, s};
-  k_reset_state<<<1, 1, 0, s>>>(P->st);
+  k_reset_state<<<1, 128, 0, s>>>(P->st, D);
   SMSM_LAUNCH_CHECK("k_reset_state");
   // b = A^H y
   T.begin(SMSM_STAGE_ADJOINT);
-  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, P->Ns * P->Nc, P->M, 1, s))) return st;
+  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, D * P->Ns * P->Nc, P->M, 1, s))) return st;
   if ((st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s))) return st;
-  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, B, P->N, 0, s))) return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, D * B, P->N, 0, s))) return st;
   T.end(SMSM_STAGE_ADJOINT);
-  if (!prm->warm) SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)B * P->N * P->N,
-                                                cudaMemcpyDeviceToDevice, s));
+  if (!prm->warm)
+    SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)D * B * P->N * P->N,
+                                  cudaMemcpyDeviceToDevice, s));
   for (int k = 0; k < prm->outer_iters; ++k) {
     T.begin(SMSM_STAGE_GRAM);
     if ((st = launch_gram(P, P->xs, P->G64, s))) return st;
@@ -219,7 +247,7 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
     T.end(SMSM_STAGE_FILTERS);
     if ((st = normal_pen_timed(P, P->xs, P->qv, lam, 0, s, &T))) return st;
     T.begin(SMSM_STAGE_CG);
-    k_cg_init<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv,
+    k_cg_init<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv,
                                           (float4*)P->pv, n4, rr0);
     SMSM_LAUNCH_CHECK("k_cg_init");
     T.end(SMSM_STAGE_CG);
@@ -230,11 +258,11 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
       double* rout = (j & 1) ? rr0 : rr1;
       if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, &T))) return st;
       T.begin(SMSM_STAGE_CG);
-      k_cg_update<<<nvb, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
+      k_cg_update<<<vg, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
                                               (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
                                               lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
       SMSM_LAUNCH_CHECK("k_cg_update");
-      k_cg_pupdate<<<nvb, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
+      k_cg_pupdate<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
       SMSM_LAUNCH_CHECK("k_cg_pupdate");
       T.end(SMSM_STAGE_CG);
     }
@@ -253,8 +281,8 @@ static bool same_params(const smsm_params* a, const smsm_params* b) { return mem
 
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
                                smsm_report* report, cudaStream_t s) {
-  const size_t nx = (size_t)P->L * P->Ns * P->N * P->N;
-  const size_t ny = (size_t)P->Ns * P->Nc * P->M * P->N;
+  const size_t nx = (size_t)P->D * P->L * P->Ns * P->N * P->N;
+  const size_t ny = (size_t)P->D * P->Ns * P->Nc * P->M * P->N;
   if (!P->has_graph || !same_params(&P->gparams, prm)) {
     if (P->has_graph) {
       cudaGraphExecDestroy(P->gexec);
@@ -296,12 +324,12 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
   SMSM_CUDA_TRY(cudaMemcpyAsync(x, P->xs, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
   if (report) {
     DevReport hr;
-    SolverState hs;
+    std::vector<SolverState> hs(P->D);
     SMSM_CUDA_TRY(cudaMemcpyAsync(&hr, P->rep, sizeof(hr), cudaMemcpyDeviceToHost, s));
-    SMSM_CUDA_TRY(cudaMemcpyAsync(&hs, P->st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    SMSM_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->st, sizeof(SolverState) * P->D, cudaMemcpyDeviceToHost, s));
     SMSM_CUDA_TRY(cudaStreamSynchronize(s));
     memset(report, 0, sizeof(*report));
-    report->status = hs.status;
+    for (int d = 0; d < P->D && !report->status; ++d) report->status = hs[d].status;
     report->outer_done = prm->outer_iters;
     const int K = prm->outer_iters < SMSM_MAX_OUTER ? prm->outer_iters : SMSM_MAX_OUTER;
     for (int k = 0; k < K; ++k) {

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsmsm.so")
 SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
 SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
+SMSM_FLAG_GENERIC_KERNELS = 1
 SMSM_MAX_OUTER = 128
 STAGES = ["adjoint", "gram", "eig", "vapply", "weights", "filters", "rowfft_inv", "column", "rowfft_fwd",
           "band", "cg"]
@@ -25,7 +26,8 @@ STAGE = {name: k for k, name in enumerate(STAGES)}
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("caipi_div", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+    _fields_ = [("caipi_div", ctypes.c_int), ("batch", ctypes.c_int), ("flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Params(ctypes.Structure):
@@ -131,14 +133,19 @@ def _dev(t: torch.Tensor, shape, name: str, dtype=torch.complex64) -> int:
 
 
 class Plan:
-    """One slice-group geometry: smsm_plan(mb, shots, coils, N, N, filter)."""
+    """One slice-group geometry: smsm_plan(mb, shots, coils, N, N, filter).
 
-    def __init__(self, mb: int, shots: int, coils: int, n: int, filter: int, caipi_div: int = 0):
+    With batch > 1 every per-problem tensor has a leading batch dimension.
+    """
+
+    def __init__(self, mb: int, shots: int, coils: int, n: int, filter: int, caipi_div: int = 0,
+                 batch: int = 1, flags: int = 0):
         self.L, self.Ns, self.Nc, self.N, self.r = mb, shots, coils, n, filter
+        self.D = batch
         self.C = shots * filter * filter
         self.M = n // shots if shots else 0
         h = ctypes.c_void_p()
-        opts = Opts(caipi_div=caipi_div)
+        opts = Opts(caipi_div=caipi_div, batch=batch, flags=flags)
         _check(lib().smsm_plan(ctypes.byref(h), mb, shots, coils, n, n, filter, ctypes.byref(opts)))
         self._h = h
 
@@ -158,13 +165,20 @@ class Plan:
         return lib().smsm_plan_workspace_bytes(self._h)
 
     # shapes
+    def _b(self, shape):
+        return (self.D,) + tuple(shape) if self.D > 1 else tuple(shape)
+
     @property
     def x_shape(self):
-        return (self.L, self.Ns, self.N, self.N)
+        return self._b((self.L, self.Ns, self.N, self.N))
 
     @property
     def y_shape(self):
-        return (self.Ns, self.Nc, self.M, self.N)
+        return self._b((self.Ns, self.Nc, self.M, self.N))
+
+    @property
+    def g_shape(self):
+        return self._b((self.L, self.C, self.C))
 
     def smsm_plan_set_sens(self, sens: torch.Tensor) -> None:
         _check(lib().smsm_plan_set_sens(self._h, _dev(sens, (self.L, self.Nc, self.N, self.N), "sens"), _stream()))
@@ -173,7 +187,7 @@ class Plan:
     set_sens = smsm_plan_set_sens
 
     def smsm_forward(self, x: torch.Tensor, phase: torch.Tensor | None = None, y: torch.Tensor | None = None):
-        xs = (self.L, 1 if phase is not None else self.Ns, self.N, self.N)
+        xs = self._b((self.L, 1 if phase is not None else self.Ns, self.N, self.N))
         if y is None:
             y = torch.empty(self.y_shape, dtype=torch.complex64, device=x.device)
         pp = _dev(phase, self.x_shape, "phase") if phase is not None else None
@@ -183,7 +197,7 @@ class Plan:
     forward = smsm_forward
 
     def smsm_adjoint(self, y: torch.Tensor, phase: torch.Tensor | None = None, x: torch.Tensor | None = None):
-        xs = (self.L, 1 if phase is not None else self.Ns, self.N, self.N)
+        xs = self._b((self.L, 1 if phase is not None else self.Ns, self.N, self.N))
         if x is None:
             x = torch.empty(xs, dtype=torch.complex64, device=y.device)
         pp = _dev(phase, self.x_shape, "phase") if phase is not None else None
@@ -194,9 +208,9 @@ class Plan:
 
     def smsm_hankel_gram(self, x: torch.Tensor, G: torch.Tensor | None = None):
         if G is None:
-            G = torch.empty((self.L, self.C, self.C), dtype=torch.complex128, device=x.device)
+            G = torch.empty(self.g_shape, dtype=torch.complex128, device=x.device)
         _check(lib().smsm_hankel_gram(self._h, _dev(x, self.x_shape, "x"),
-                                      _dev(G, (self.L, self.C, self.C), "G", torch.complex128), _stream()))
+                                      _dev(G, self.g_shape, "G", torch.complex128), _stream()))
         return G
 
     hankel_gram = smsm_hankel_gram
@@ -204,7 +218,7 @@ class Plan:
     def smsm_apply_filters(self, W: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None):
         if out is None:
             out = torch.empty(self.x_shape, dtype=torch.complex64, device=x.device)
-        _check(lib().smsm_apply_filters(self._h, _dev(W, (self.L, self.C, self.C), "W", torch.complex128),
+        _check(lib().smsm_apply_filters(self._h, _dev(W, self.g_shape, "W", torch.complex128),
                                         _dev(x, self.x_shape, "x"), _dev(out, self.x_shape, "out"), _stream()))
         return out
 

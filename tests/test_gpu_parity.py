@@ -239,3 +239,72 @@ def test_errors_do_not_abort(smsm):
     with pytest.raises(smsm.SmsmError) as e:
         p2.forward(x)
     assert e.value.status == smsm.SMSM_ERR_STATE
+
+
+def test_batch_matches_single_problems(smsm):
+    # D independent problems (diffusion directions sharing coil maps) in one plan:
+    # every operator and the whole solve must match the per-problem results.
+    key = "tiny"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    D = 3
+    rng = np.random.default_rng(21)
+    S = crandn(rng, L, Nc, N, N) / np.sqrt(Nc)
+    xb = crandn(rng, D, L, Ns, N, N)
+    yb = crandn(rng, D, Ns, Nc, N // Ns, N)
+    Wb = np.stack([_random_weight(rng, L, Ns * r * r) for _ in range(D)])
+    pb = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    pb.set_sens(c64(S))
+    fwd = pb.forward(c64(xb)).cpu().numpy()
+    adj = pb.adjoint(c64(yb)).cpu().numpy()
+    G = pb.hankel_gram(c64(xb)).cpu().numpy()
+    pen = pb.apply_filters(c128(Wb), c64(xb)).cpu().numpy()
+    for d in range(D):
+        assert O.nrmse(fwd[d], O.forward(xb[d], S, Ldiv=Ldiv)) < OP_TOL
+        assert O.nrmse(adj[d], O.adjoint(yb[d], S, L, Ldiv=Ldiv)) < OP_TOL
+        assert O.nrmse(G[d], O.gram(xb[d].astype(np.complex64).astype(complex), r)) < OP_TOL
+        ref = O.penalty(xb[d].astype(np.complex64).astype(complex), Wb[d].astype(np.complex64).astype(complex), r)
+        assert O.nrmse(pen[d], ref) < OP_TOL
+    # whole solve: each direction against its own single-problem plan
+    g, xt, y0 = _problem(key, 5)
+    ys = np.stack([y0 * np.exp(1j * 0.3 * d) + 0.05 * crandn(rng, *y0.shape) for d in range(D)])
+    prm = smsm.default_params(lam=1e-2, outer_iters=4, cg_iters=5)
+    pb2 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    pb2.set_sens(c64(g["sens"]))
+    xb_out, rep = pb2.reconstruct(c64(ys), params=prm)
+    assert rep.status == 0
+    p1 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv)
+    p1.set_sens(c64(g["sens"]))
+    for d in range(D):
+        x1, _ = p1.reconstruct(c64(ys[d]), params=prm)
+        assert O.nrmse(xb_out[d].cpu().numpy(), x1.cpu().numpy()) < 1e-4
+    ref = O.reconstruct(ys[D - 1], g["sens"], r, dict(K=4, J=5, lam=1e-2), Ldiv=Ldiv)
+    assert O.nrmse(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
+
+
+@pytest.mark.parametrize("L,Ns,Nc,N,r", [
+    (2, 4, 8, 64, 5),    # M = 16 (lane segments)
+    (3, 8, 6, 64, 3),    # M = 8, three slices
+    (2, 4, 8, 128, 6),   # M = 32
+    (2, 2, 6, 128, 4),   # M = 64 (local radix-2)
+    (1, 2, 4, 192, 4),   # M = 96 (local radix-3), one slice
+    (3, 2, 4, 256, 4),   # M = 128 (local radix-4)
+    (1, 3, 5, 96, 3),    # N = 96, M = 32
+])
+def test_fast_column_stage_matches_generic(smsm, L, Ns, Nc, N, r):
+    # the warp-shuffle column stage and the shape-generic one compute the same
+    # (A^H A + lambda P_W); compare whole (short) solves, and one against the oracle
+    rng = np.random.default_rng(L * 100 + N + Ns)
+    S = crandn(rng, L, Nc, N, N) / np.sqrt(Nc)
+    y = crandn(rng, Ns, Nc, N // Ns, N)
+    prm = smsm.default_params(lam=3e-2, outer_iters=2, cg_iters=3)
+    out = []
+    for flags in (0, smsm.SMSM_FLAG_GENERIC_KERNELS):
+        p = smsm.Plan(L, Ns, Nc, N, r, flags=flags)
+        p.set_sens(c64(S))
+        x, rep = p.reconstruct(c64(y), params=prm)
+        assert rep.status == 0
+        out.append(x.cpu().numpy())
+    assert O.nrmse(out[0], out[1]) < 1e-5
+    if N <= 128:
+        ref = O.reconstruct(y, S, r, dict(K=2, J=3, lam=3e-2))
+        assert O.nrmse(out[0], ref) < 1e-4
