@@ -180,28 +180,37 @@ class Clocks:
 # our arm
 # ---------------------------------------------------------------------------
 
-def stage_work(cfg):
-    """Algorithmic work of one launch (bracket) of each kernel class."""
+def stage_work(cfg, D, sweeps):
+    """Algorithmic work of one launch (bracket) of each kernel class, over a batch of D problems.
+
+    Returns {stage: (bound, amount)} with bound "alu" (FP32 flops) or "hbm" (bytes)."""
     L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
     B, NN, M, C = L * Ns, N * N, N // Ns, Ns * r * r
+    Cp = C + (C & 1)
+    half = Cp // 2
     P = (N - r + 1) ** 2
     R2 = 2 * r - 1
     nband = NN - (N - 2 * (r - 1)) ** 2
     lg = np.log2
-    # column stage flops: per x line, per coil and slice-shot: coil x twiddle multiply
-    # (2 cmul/px), fold (1 cadd/px), forward + inverse M-point FFT (5 M log2 M each),
-    # CAIPI combine + back-projection (2 cmul/line), conj multiply-accumulate (2 cmul + cadd/px);
-    # plus the two N-point FFTs per slice-shot line and the Ns x Ns multiplier.
-    col_flops = N * (Nc * B * (6 * N * 2 + 2 * N + 2 * 5 * M * lg(M) + 2 * 8 * M + 6 * N * 2 + 2 * N)
-                     + B * 2 * 5 * N * lg(N) + B * Ns * 8 * N)
+    # column stage, per image column and coil: coil x shot-twiddle multiply (6 flops) and
+    # multiply-accumulate into the fold (8) per pixel, forward + inverse M-point FFT
+    # (5 M log2 M each), CAIPI combine + back-projection (8 + 6 per line sample and slice),
+    # unfold multiply-accumulate (6 + 8 per pixel); per column: two N-point FFTs per line
+    # and the Ns x Ns multiplier (8 Ns per pixel and line).
+    col = N * (Nc * L * Ns * (14 * N + 2 * 5 * M * lg(M) + 14 * M + 14 * N)
+               + B * 2 * 5 * N * lg(N) + B * 8 * Ns * N)
     return {
-        "column": {"bytes": 8 * NN * (L * Nc + 2 * B + L * Ns * Ns), "flops": col_flops},
-        "rowfft_inv": {"bytes": 2 * 8 * B * NN, "flops": B * N * 5 * N * lg(N)},
-        "rowfft_fwd": {"bytes": 2 * 8 * B * NN, "flops": B * N * 5 * N * lg(N)},
-        "band": {"bytes": 8 * 2 * L * Ns * nband, "flops": 8 * 2 * L * nband * Ns * Ns * R2 * R2},
-        "cg": {"bytes": 9 * 8 * B * NN, "flops": 10 * B * NN},
-        "gram": {"bytes": 8 * B * NN, "flops": 8 * L * P * C * (C + 1) / 2},
-        "eig": {"bytes": 16 * L * C * C, "flops": None},
+        "column": ("alu", D * col),
+        "band": ("alu", D * 8 * L * nband * Ns * Ns * R2 * R2),
+        "gram": ("alu", D * 8 * L * P * C * (C + 1) / 2),
+        "eig": ("alu", D * L * sweeps * (Cp - 1) * (half * (half + 1) / 2) * 96),
+        "vapply": ("alu", D * L * sweeps * (Cp - 1) * half * C * 18),
+        "rowfft_inv": ("hbm", D * 2 * 8 * B * NN),
+        "rowfft_fwd": ("hbm", D * 2 * 8 * B * NN),
+        "cg": ("hbm", D * 9 * 8 * B * NN),
+        "weights": ("alu", D * L * 8 * C * C * C),
+        "filters": ("alu", D * L * (R2 * R2 + 1) * Ns * Ns * R2 * R2 * r * r * 2 + D * L * Ns * Ns * NN * R2 * 8),
+        "adjoint": ("hbm", D * 8 * (L * Nc * NN + 2 * Ns * Nc * M * N + 2 * B * NN)),
     }
 
 
@@ -318,23 +327,21 @@ def run_ours(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
-    work = stage_work(cfg).get(dominant, {"bytes": None, "flops": None})
+    sweeps = float(np.mean([rep.sweeps[k] for k in range(cfg["K"])]))
+    bound, amount = stage_work(cfg, D, sweeps)[dominant]
     per_launch_ms = dom_ms / max(dom_n, 1)
     sm_mhz = clocks.get("sm_mhz") or 1455.0
-    if dominant in ("column", "band", "gram") and work["flops"]:
+    if bound == "alu":
         # FP32 ALU bound: 152 SMs x 128 FP32 lanes x 2 flops x the SM clock sampled under load
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = work["flops"] / (per_launch_ms * 1e-3) / 1e12
+        achieved = amount / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms,
-                "peak_note": f"FP32 FMA peak at the sampled median SM clock {sm_mhz:.0f} MHz"}
-    elif work["bytes"]:
-        achieved = work["bytes"] / (per_launch_ms * 1e-3) / 1e9
+                "peak_note": f"FP32 FMA peak (152 SMs x 128 lanes x 2) at the sampled median SM clock {sm_mhz:.0f} MHz"}
+    else:
+        achieved = amount / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms, "peak_note": peak_src}
-    else:
-        roof = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-                "kernel": dominant, "launch_ms": per_launch_ms}
 
     # CPU baseline: the oracle as it stands, on a bounded sample of the same workload
     cpu = None
@@ -352,7 +359,8 @@ def run_ours(args):
         "config": {"workload": workload_desc(cfg, D), "form": "plain FP32 (FP64 reductions)",
                    "directions_per_step": D,
                    "l2": "flushed before every step (512 MB write)", "parallelism": f"replicas x{world}",
-                   "lambda": LAM, "stages_ms_first_warmup": stages_all},
+                   "lambda": LAM, "stages_ms_first_warmup": stages_all,
+                   "jacobi_sweeps_per_outer": [rep.sweeps[k] for k in range(cfg["K"])]},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": world * D * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),

@@ -96,7 +96,9 @@ typedef struct {
   int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 15 */
   int timing;         /* bitmask of (1 << smsm_stage): bracket those launches with CUDA
                          events inside the solve and report their device time */
-  int reserved[5];
+  int eig_cold;       /* 1: restart the eigensolver from scratch every outer iteration
+                         (default 0: start from the previous iteration's eigenvectors) */
+  int reserved[4];
 } smsm_params;
 
 #define SMSM_MAX_OUTER 128

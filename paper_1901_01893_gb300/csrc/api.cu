@@ -94,7 +94,7 @@ static void free_plan(smsm_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->twN,  P->twM,  P->tw_shot, P->cph,  P->Etab,  P->sensT, P->hA,   P->hB,
                   P->yh,   P->phaseT, P->xs,    P->bv,   P->rv,    P->pv,    P->qv,   P->ybuf,
-                  P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper,
+                  P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2,
                   P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -137,7 +137,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   const int C = shots * r * r;
   const int Cp = C + (C & 1);
   if (C > SMSM_MAX_C || eig_jacobi_smem(Cp) > 227 * 1024) {
-    smsm_set_error("smsm_plan: shots*filter^2 = %d is above the eigensolver's shared-memory limit (160)", C);
+    smsm_set_error("smsm_plan: shots*filter^2 = %d is above the eigensolver's shared-memory limit (166)", C);
     return SMSM_ERR_ARG;
   }
   const int caipi_div = (opts && opts->caipi_div > 0) ? opts->caipi_div : mb;
@@ -205,6 +205,8 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(sweeps, LD);
   A(V, LD * C * C);
   A(Wf, LD * C * C);
+  A(Gw, LD * C * C);
+  A(Gw2, LD * C * C);
   A(wper, LD * shots * shots * R2 * R2);
   A(wcls, LD * R2 * R2 * shots * shots * R2 * R2);
   A(multT, LD * shots * shots * NN);
@@ -266,6 +268,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   }
   if (!st) st = operators_init_attrs();
   if (!st) st = colfast_init_attrs();
+  if (!st) st = band_init_attrs(P);
   if (!st) st = eig_init_attrs(Cp);
   if (!st && smsm_col_smem_bytes(P) > 200 * 1024) {
     smsm_set_error("smsm_plan: column stage would need %zu bytes of shared memory", smsm_col_smem_bytes(P));

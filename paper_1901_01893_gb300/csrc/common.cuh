@@ -98,9 +98,10 @@ struct smsm_plan_s {
   float* eig;        // [L][Cp]
   float4* rotlog;    // [L][SMSM_MAX_SWEEPS][Cp-1][Cp/2]
   int* sweeps;       // [L]
-  float2 *V, *Wf;    // [L][C][C]
+  float2 *V, *Wf;    // [LD][C][C]
+  float2 *Gw, *Gw2;  // [LD][C][C] warm-start congruence V^H G V (and its half product)
   float2* wper;      // [L][Ns][Ns][R2*R2]
-  float2* wcls;      // [L][R2*R2][Ns][Ns][R2*R2]
+  float2* wcls;      // [LD][R2*R2 classes][Ns (i')][R2*R2 taps][Ns (i)] border correction taps
   float2* multT;     // [L][Ns][Ns][N(x)][N(y)]
   double *part_pq_col, *part_pq_band, *part_rr;  // partial sums [D][PART]; part_rr: [2 banks][D][PART]
   SolverState* st;   // [D]
@@ -228,6 +229,7 @@ size_t eig_jacobi_smem(int Cp);
 smsm_status operators_init_attrs();
 size_t smsm_col_smem_bytes(const smsm_plan_s* P);
 int band_blocks(const smsm_plan_s* P);
+smsm_status band_init_attrs(const smsm_plan_s* P);
 // solver.cu
 int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,

@@ -37,27 +37,50 @@ __device__ __forceinline__ void jpair(int round, int k, int Cp, int& p, int& q) 
 
 __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z == 1.f && J.w == 0.f; }
 
-// J = [[c, s], [-s e, c e]],  e = exp(-i phi) = (er, ei), phi = arg(G_pq)
-__global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, float* __restrict__ eig,
-                                                 float4* __restrict__ rlog, int* __restrict__ sweeps_out, int C,
-                                                 int Cp, int max_sweeps, float tol) {
+// J = [[c, s], [-s e, c e]],  e = exp(-i phi) = (er, ei), phi = arg(G_pq).
+// G lives in shared memory with row stride Cp+1 (odd, so column walks hit
+// distinct banks).  Each round: C/2 threads compute the rotations of the
+// round-robin pairs (p_k, q_k) into shared tables; then every 2x2 block
+// (k1 <= k2) is transformed as J_k1^H B J_k2, its mirror (k2, k1) written as
+// the conjugate transpose (G stays exactly Hermitian), and the diagonal blocks
+// are set to their analytic result diag(a - t|b|, d + t|b|).
+// warm != 0: start from Gw = V_prev^H G V_prev (symmetrised on load).
+__global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, const float2* __restrict__ Gw,
+                                                 float* __restrict__ eig, float4* __restrict__ rlog,
+                                                 int* __restrict__ sweeps_out, int C, int Cp, int max_sweeps,
+                                                 float tol) {
   extern __shared__ float2 g[];
-  float4* rot = reinterpret_cast<float4*>(g + (size_t)Cp * Cp);
+  const int ld = Cp + 1;
+  const int half = Cp / 2;
+  float4* rot = reinterpret_cast<float4*>(g + (size_t)Cp * ld + ((Cp * ld) & 1));
+  int* rp = reinterpret_cast<int*>(rot + half);
+  int* rq = rp + half;
   __shared__ int nrot;
   __shared__ float dmax;
   const int l = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const double2* Gl = G + (size_t)l * C * C;
+  const float2* Gwl = Gw ? Gw + (size_t)l * C * C : nullptr;
   for (int e = tid; e < Cp * Cp; e += nt) {
-    int a = e / Cp, b = e - a * Cp;
-    g[e] = (a < C && b < C) ? cmk((float)Gl[(size_t)a * C + b].x, (float)Gl[(size_t)a * C + b].y) : cmk(0.f, 0.f);
+    const int a = e / Cp, b = e - a * Cp;
+    float2 v = cmk(0.f, 0.f);
+    if (a < C && b < C) {
+      if (Gwl) {
+        const float2 u = Gwl[(size_t)a * C + b], w = Gwl[(size_t)b * C + a];
+        v = cmk(0.5f * (u.x + w.x), 0.5f * (u.y - w.y));
+        if (a == b) v.y = 0.f;
+      } else {
+        v = cmk((float)Gl[(size_t)a * C + b].x, (float)Gl[(size_t)a * C + b].y);
+      }
+    }
+    g[a * ld + b] = v;
   }
   if (tid == 0) dmax = 0.f;
   __syncthreads();
-  if (tid < Cp) atomicMax(reinterpret_cast<int*>(&dmax), __float_as_int(fmaxf(g[tid * Cp + tid].x, 0.f)));
+  if (tid < Cp) atomicMax(reinterpret_cast<int*>(&dmax), __float_as_int(fmaxf(g[tid * ld + tid].x, 0.f)));
   __syncthreads();
   // rotations below this absolute size only churn rounding noise
   const float floor_abs = 1e-7f * dmax;
-  const int half = Cp / 2;
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
     if (tid == 0) nrot = 0;
@@ -66,8 +89,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
       if (tid < half) {
         int p, q;
         jpair(round, tid, Cp, p, q);
-        const float a = g[p * Cp + p].x, d = g[q * Cp + q].x;
-        const float2 b = g[p * Cp + q];
+        rp[tid] = p;
+        rq[tid] = q;
+        const float a = g[p * ld + p].x, d = g[q * ld + q].x;
+        const float2 b = g[p * ld + q];
         const float babs = hypotf(b.x, b.y);
         float4 J = make_float4(1.f, 0.f, 1.f, 0.f);
         if (babs > floor_abs && babs > tol * sqrtf(fabsf(a * d))) {
@@ -81,37 +106,48 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
         rlog[(((size_t)l * SMSM_MAX_SWEEPS + sw) * (Cp - 1) + round) * half + tid] = J;
       }
       __syncthreads();
-      for (int blk = tid; blk < half * half; blk += nt) {
-        const int k1 = blk / half, k2 = blk - k1 * half;
-        const float4 J1 = rot[k1], J2 = rot[k2];
-        if (is_ident(J1) && is_ident(J2)) continue;
-        int p1, q1, p2, q2;
-        jpair(round, k1, Cp, p1, q1);
-        jpair(round, k2, Cp, p2, q2);
-        float2 B00 = g[p1 * Cp + p2], B01 = g[p1 * Cp + q2];
-        float2 B10 = g[q1 * Cp + p2], B11 = g[q1 * Cp + q2];
-        // T = J1^H B : row0 = c B0 - s conj(e1) B1 ; row1 = s B0 + c conj(e1) B1
+      for (int k1 = warp; k1 < half; k1 += nwarp) {
+        const float4 J1 = rot[k1];
+        const bool id1 = is_ident(J1);
+        const int p1 = rp[k1], q1 = rq[k1];
         const float2 e1c = cmk(J1.z, -J1.w);
-        float2 T00 = csub(cscale(B00, J1.x), cscale(cmul(e1c, B10), J1.y));
-        float2 T01 = csub(cscale(B01, J1.x), cscale(cmul(e1c, B11), J1.y));
-        float2 T10 = cadd(cscale(B00, J1.y), cscale(cmul(e1c, B10), J1.x));
-        float2 T11 = cadd(cscale(B01, J1.y), cscale(cmul(e1c, B11), J1.x));
-        // O = T J2 : col0 = c T0 - s e2 T1 ; col1 = s T0 + c e2 T1
-        const float2 e2 = cmk(J2.z, J2.w);
-        float2 O00 = csub(cscale(T00, J2.x), cscale(cmul(T01, e2), J2.y));
-        float2 O10 = csub(cscale(T10, J2.x), cscale(cmul(T11, e2), J2.y));
-        float2 O01 = cadd(cscale(T00, J2.y), cscale(cmul(T01, e2), J2.x));
-        float2 O11 = cadd(cscale(T10, J2.y), cscale(cmul(T11, e2), J2.x));
-        if (k1 == k2) {
-          O01 = cmk(0.f, 0.f);
-          O10 = cmk(0.f, 0.f);
-          O00.y = 0.f;
-          O11.y = 0.f;
+        for (int k2 = k1 + lane; k2 < half; k2 += 32) {
+          const float4 J2 = rot[k2];
+          if (k2 == k1) {
+            if (id1) continue;
+            const float a = g[p1 * ld + p1].x, d = g[q1 * ld + q1].x;
+            const float2 b = g[p1 * ld + q1];
+            const float tb = (J1.y / J1.x) * hypotf(b.x, b.y);
+            g[p1 * ld + p1] = cmk(a - tb, 0.f);
+            g[q1 * ld + q1] = cmk(d + tb, 0.f);
+            g[p1 * ld + q1] = cmk(0.f, 0.f);
+            g[q1 * ld + p1] = cmk(0.f, 0.f);
+            continue;
+          }
+          if (id1 && is_ident(J2)) continue;
+          const int p2 = rp[k2], q2 = rq[k2];
+          const float2 B00 = g[p1 * ld + p2], B01 = g[p1 * ld + q2];
+          const float2 B10 = g[q1 * ld + p2], B11 = g[q1 * ld + q2];
+          // T = J1^H B : row0 = c B0 - s conj(e1) B1 ; row1 = s B0 + c conj(e1) B1
+          const float2 T00 = csub(cscale(B00, J1.x), cscale(cmul(e1c, B10), J1.y));
+          const float2 T01 = csub(cscale(B01, J1.x), cscale(cmul(e1c, B11), J1.y));
+          const float2 T10 = cadd(cscale(B00, J1.y), cscale(cmul(e1c, B10), J1.x));
+          const float2 T11 = cadd(cscale(B01, J1.y), cscale(cmul(e1c, B11), J1.x));
+          // O = T J2 : col0 = c T0 - s e2 T1 ; col1 = s T0 + c e2 T1
+          const float2 e2 = cmk(J2.z, J2.w);
+          const float2 O00 = csub(cscale(T00, J2.x), cscale(cmul(T01, e2), J2.y));
+          const float2 O10 = csub(cscale(T10, J2.x), cscale(cmul(T11, e2), J2.y));
+          const float2 O01 = cadd(cscale(T00, J2.y), cscale(cmul(T01, e2), J2.x));
+          const float2 O11 = cadd(cscale(T10, J2.y), cscale(cmul(T11, e2), J2.x));
+          g[p1 * ld + p2] = O00;
+          g[p1 * ld + q2] = O01;
+          g[q1 * ld + p2] = O10;
+          g[q1 * ld + q2] = O11;
+          g[p2 * ld + p1] = conjf2(O00);
+          g[q2 * ld + p1] = conjf2(O01);
+          g[p2 * ld + q1] = conjf2(O10);
+          g[q2 * ld + q1] = conjf2(O11);
         }
-        g[p1 * Cp + p2] = O00;
-        g[p1 * Cp + q2] = O01;
-        g[q1 * Cp + p2] = O10;
-        g[q1 * Cp + q2] = O11;
       }
       __syncthreads();
     }
@@ -119,20 +155,31 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
     __syncthreads();
     if (done) break;
   }
-  for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * Cp + j].x;
+  for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
 }
 
-// V = product of the logged rotations; one warp per row of V.
+// V = V0 * (product of the logged rotations), V0 = I or the previous V (warm).
+// One CTA per (matrix, 32 rows); each warp owns 4 rows in shared memory and
+// applies every round's rotations to them, reading each rotation once.
+#define VA_ROWS_PER_WARP 4
 __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog, const int* __restrict__ sweeps,
-                                                float2* __restrict__ V, int C, int Cp) {
+                                                float2* __restrict__ V, int C, int Cp, int warm) {
   extern __shared__ float2 rows[];
   const int l = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.y * 8 + w;
-  if (t >= C) return;
-  float2* row = rows + w * Cp;
-  for (int j = lane; j < Cp; j += 32) row[j] = cmk(j == t ? 1.f : 0.f, 0.f);
+  const int t0 = blockIdx.y * 32 + w * VA_ROWS_PER_WARP;
+  float2* myrows = rows + (size_t)w * VA_ROWS_PER_WARP * Cp;
+  float2* Vl = V + (size_t)l * C * C;
+#pragma unroll
+  for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
+    const int t = t0 + rr;
+    for (int j = lane; j < Cp; j += 32) {
+      float2 v = cmk(0.f, 0.f);
+      if (t < C && j < C) v = warm ? Vl[(size_t)t * C + j] : cmk(j == t ? 1.f : 0.f, 0.f);
+      myrows[rr * Cp + j] = v;
+    }
+  }
   __syncwarp();
   const int nsw = sweeps[l];
   const int half = Cp / 2;
@@ -144,16 +191,62 @@ __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog,
         if (is_ident(J)) continue;
         int p, q;
         jpair(round, k, Cp, p, q);
-        const float2 vp = row[p], vq = row[q];
-        const float2 evq = cmul(cmk(J.z, J.w), vq);
-        row[p] = csub(cscale(vp, J.x), cscale(evq, J.y));
-        row[q] = cadd(cscale(vp, J.y), cscale(evq, J.x));
+        const float2 e = cmk(J.z, J.w);
+#pragma unroll
+        for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
+          float2* row = myrows + rr * Cp;
+          const float2 vp = row[p], vq = row[q];
+          const float2 evq = cmul(e, vq);
+          row[p] = csub(cscale(vp, J.x), cscale(evq, J.y));
+          row[q] = cadd(cscale(vp, J.y), cscale(evq, J.x));
+        }
       }
       __syncwarp();
     }
   }
-  float2* Vr = V + ((size_t)l * C + t) * C;
-  for (int j = lane; j < C; j += 32) Vr[j] = row[j];
+#pragma unroll
+  for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
+    const int t = t0 + rr;
+    if (t >= C) continue;
+    for (int j = lane; j < C; j += 32) Vl[(size_t)t * C + j] = myrows[rr * Cp + j];
+  }
+}
+
+// Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
+// step 0: T = G V (G in FP64, rounded on load); step 1: Gw = V^H T.
+#define CG_T 16
+__global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ G, const float2* __restrict__ V,
+                                                    const float2* __restrict__ Tin, float2* __restrict__ out, int C,
+                                                    int step) {
+  __shared__ float2 As[CG_T][CG_T + 1];
+  __shared__ float2 Bs[CG_T][CG_T + 1];
+  const int l = blockIdx.z;
+  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
+  const int a = blockIdx.y * CG_T + ty, b = blockIdx.x * CG_T + tx;
+  const size_t off = (size_t)l * C * C;
+  float2 acc = cmk(0.f, 0.f);
+  for (int k0 = 0; k0 < C; k0 += CG_T) {
+    // A tile: rows a-block, cols k;  B tile: rows k, cols b-block
+    const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
+    const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
+    float2 av = cmk(0.f, 0.f), bv = cmk(0.f, 0.f);
+    if (ar < C && ak < C) {
+      if (step == 0) {
+        const double2 gv = G[off + (size_t)ar * C + ak];
+        av = cmk((float)gv.x, (float)gv.y);
+      } else {
+        av = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
+      }
+    }
+    if (bk < C && bc < C) bv = step == 0 ? V[off + (size_t)bk * C + bc] : Tin[off + (size_t)bk * C + bc];
+    As[ty][tx] = av;
+    Bs[ty][tx] = bv;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
+    __syncthreads();
+  }
+  if (a < C && b < C) out[off + (size_t)a * C + b] = acc;
 }
 
 // eps schedule and report, one CTA per direction d: eps_1 = eps0_rel * (largest
@@ -233,7 +326,10 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
   }
 }
 
-static size_t jacobi_smem(int Cp) { return (size_t)Cp * Cp * sizeof(float2) + (size_t)(Cp / 2) * sizeof(float4); }
+static size_t jacobi_smem(int Cp) {
+  const size_t gsz = (size_t)Cp * (Cp + 1) + (((size_t)Cp * (Cp + 1)) & 1);  // float2, keep 16-byte alignment
+  return gsz * sizeof(float2) + (size_t)(Cp / 2) * (sizeof(float4) + 2 * sizeof(int));
+}
 
 smsm_status eig_init_attrs(int Cp) {
   size_t sm = jacobi_smem(Cp);
@@ -249,24 +345,35 @@ size_t eig_jacobi_smem(int Cp) { return jacobi_smem(Cp); }
 
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T) {
-  const int Cp = P->Cp;
+  const int Cp = P->Cp, C = P->C;
   int msw = prm->max_sweeps > 0 ? prm->max_sweeps : 15;
   if (msw > SMSM_MAX_SWEEPS) msw = SMSM_MAX_SWEEPS;
+  // warm start from the previous outer iteration's eigenvectors (same solve)
+  const int warm = (outer > 0 && !prm->eig_cold) ? 1 : 0;
   if (T) T->begin(SMSM_STAGE_EIG);
-  k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, P->eig, P->rotlog, P->sweeps, P->C, Cp, msw, 1e-6f);
+  if (warm) {
+    dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
+    SMSM_LAUNCH_CHECK("k_congruence");
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw2, C, 1);
+    SMSM_LAUNCH_CHECK("k_congruence");
+  }
+  k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->rotlog, P->sweeps, C, Cp,
+                                                 msw, 1e-6f);
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  dim3 gv(P->LD, (P->C + 7) / 8);
-  k_vapply<<<gv, 256, (size_t)8 * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, P->C, Cp);
+  dim3 gv(P->LD, (C + 31) / 32);
+  k_vapply<<<gv, 256, (size_t)8 * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
+                                                                              warm);
   SMSM_LAUNCH_CHECK("k_vapply");
   if (T) T->end(SMSM_STAGE_VAPPLY);
   if (T) T->begin(SMSM_STAGE_WEIGHTS);
-  k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, P->C, Cp, outer, prm->eps0_rel, prm->eta,
-                          prm->eps_min_rel);
+  k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, C, Cp, outer, prm->eps0_rel, prm->eta,
+                             prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
-  dim3 gw(P->LD, (P->C + 15) / 16);
-  k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->C, Cp, prm->mode, prm->rank, P->L);
+  dim3 gw(P->LD, (C + 15) / 16);
+  k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
   SMSM_LAUNCH_CHECK("k_weights");
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;

@@ -146,38 +146,50 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
 //   class c in [0, R2) per axis, R2 = 2r-1: c < r-1 -> pixel c from the low
 //   edge; c == r-1 -> interior; c > r-1 -> pixel N-r + (c-(r-1)) near the
 //   high edge.  Valid patch offsets p in [max(0, c-(r-1)), min(r-1, c)].
-//   wcls[l][cy*R2+cx][i][i'][d], wper[l][i][i'][d] (= the interior class),
-//   d = (dy + r-1)*R2 + (dx + r-1).
+//   wper[l][i][i'][d]: periodic (interior) filter, d = (dy + r-1)*R2 + (dx + r-1).
+//   dcls[l][cls][i'][d][i]: the border correction taps of class cls,
+//     (tap in range ? class filter : 0) - periodic filter, applied to the
+//     periodically wrapped x:  corr_i[n] = sum_{i',d} dcls * x_i'[(n + d) mod N].
+//   A tap (dy, dx) is in range for class (cy, cx) when the pixel plus the tap
+//   stays inside [0, N): dy >= -cy for low classes, dy <= 2r-2-cy for high ones.
 // ---------------------------------------------------------------------------
-__global__ void k_filters(const float2* __restrict__ W, float2* __restrict__ wcls, float2* __restrict__ wper, int Ns,
+__global__ void k_filters(const float2* __restrict__ W, float2* __restrict__ dcls, float2* __restrict__ wper, int Ns,
                           int r, int C) {
   const int R2 = 2 * r - 1;
-  const int cls = blockIdx.x;  // 0..R2*R2 (last = periodic copy)
+  const int cls = blockIdx.x;  // 0..R2*R2 (last = periodic filter)
   const int ij = blockIdx.y;
   const int l = blockIdx.z;
   const int i = ij / Ns, j = ij - i * Ns;
   const bool per = (cls == R2 * R2);
   const int cy = per ? r - 1 : cls / R2, cx = per ? r - 1 : cls % R2;
-  const int ly = max(0, cy - (r - 1)), hy = min(r - 1, cy);
-  const int lx = max(0, cx - (r - 1)), hx = min(r - 1, cx);
   const float2* Wl = W + (size_t)l * C * C;
   const int rr = r * r;
   for (int d = threadIdx.x; d < R2 * R2; d += blockDim.x) {
     const int dy = d / R2 - (r - 1), dx = d % R2 - (r - 1);
-    float2 s = cmk(0.f, 0.f);
-    for (int py = ly; py <= hy; ++py) {
+    // periodic filter: all p with q = p + d in the filter support
+    float2 sp = cmk(0.f, 0.f);
+    float2 sc = cmk(0.f, 0.f);
+    const int ly = max(0, cy - (r - 1)), hy = min(r - 1, cy);
+    const int lx = max(0, cx - (r - 1)), hx = min(r - 1, cx);
+    for (int py = 0; py < r; ++py) {
       const int qy = py + dy;
       if (qy < 0 || qy >= r) continue;
-      for (int px = lx; px <= hx; ++px) {
+      for (int px = 0; px < r; ++px) {
         const int qx = px + dx;
         if (qx < 0 || qx >= r) continue;
-        s = cadd(s, Wl[(size_t)(j * rr + qy * r + qx) * C + (i * rr + py * r + px)]);
+        const float2 w = Wl[(size_t)(j * rr + qy * r + qx) * C + (i * rr + py * r + px)];
+        sp = cadd(sp, w);
+        if (py >= ly && py <= hy && px >= lx && px <= hx) sc = cadd(sc, w);
       }
     }
-    if (per)
-      wper[((size_t)(l * Ns + i) * Ns + j) * R2 * R2 + d] = s;
-    else
-      wcls[(((size_t)l * R2 * R2 + cls) * Ns * Ns + ij) * R2 * R2 + d] = s;
+    if (per) {
+      wper[((size_t)(l * Ns + i) * Ns + j) * R2 * R2 + d] = sp;
+    } else {
+      const bool iny = (cy < r - 1) ? (dy >= -cy) : (cy > r - 1 ? dy <= 2 * r - 2 - cy : true);
+      const bool inx = (cx < r - 1) ? (dx >= -cx) : (cx > r - 1 ? dx <= 2 * r - 2 - cx : true);
+      const float2 v = (iny && inx) ? csub(sc, sp) : cscale(sp, -1.f);
+      dcls[((((size_t)l * R2 * R2 + cls) * Ns + j) * R2 * R2 + d) * Ns + i] = v;
+    }
   }
 }
 
@@ -225,7 +237,7 @@ smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2*
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s) {
   const int R2 = P->R2;
   dim3 g1(R2 * R2 + 1, P->Ns * P->Ns, P->LD);
-  k_filters<<<g1, 128, 0, s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C);
+  k_filters<<<g1, 128, 0, s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C);  // wcls holds the class taps dcls
   SMSM_LAUNCH_CHECK("k_filters");
   dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->LD);
   k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
@@ -235,95 +247,198 @@ smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s
 
 // ---------------------------------------------------------------------------
 // Border band: out[n] += scale * (P_valid(x)[n] - P_periodic(x)[n]) for the
-// pixels within r-1 of an edge; optional partial of Re<x, scale*corr>.
+// pixels within r-1 of an edge, with the per-class taps dcls; optional
+// per-CTA partial of Re<x, scale*corr>.
+// The band is four strips: top (rows 0..r-2) and bottom (rows N-r+1..N-1) over
+// all columns, left/right (columns 0..r-2, N-r+1..N-1) over the interior rows.
+// A CTA takes BAND_TX pixels of one strip line, stages the (periodically
+// wrapped) x window of every shot and the line's class taps in shared memory,
+// and each thread accumulates all Ns output shots of its pixel.  Pixels at the
+// ends of a top/bottom line (the corners) have their own class and read their
+// taps from global memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void band_pixel(int b, int N, int r, int& ny, int& nx) {
-  const int w = r - 1;
-  const int top = 2 * w * N;
-  if (b < top) {
-    int row = b / N;
-    nx = b - row * N;
-    ny = row < w ? row : N - w + (row - w);
-  } else {
-    int b2 = b - top;
-    int row = b2 / (2 * w), c = b2 - row * (2 * w);
-    ny = w + row;
-    nx = c < w ? c : N - w + (c - w);
-  }
-}
+#define BAND_P 2                  // pixels per thread
+#define BAND_TX (32 * BAND_P)     // pixels per strip line per CTA
 
-__device__ __forceinline__ int pix_class(int n, int N, int r) {
-  if (n < r - 1) return n;
-  if (n <= N - r) return r - 1;
-  return r - 1 + (n - (N - r));
-}
-
+// One CTA = one chunk of BAND_TX pixels of one line of one strip; warp j sums
+// the taps of input shot j for every output shot; the NS partials of each
+// (pixel, output shot) are then added in a fixed order (deterministic).  The
+// line's window of x (2r-1 lines across, BAND_TX + 2r-2 along, periodically
+// wrapped) is staged in shared memory as [shot][across][along] for both
+// orientations; taps are warp-uniform loads (L1 broadcast).
+template <int NS>
 __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, float2* __restrict__ out,
-                                              const float2* __restrict__ wper, const float2* __restrict__ wcls,
-                                              int L, int Ns, int N, int r, int nband, float scale,
+                                              const float2* __restrict__ dcls, int L, int N, int r, float scale,
                                               double* __restrict__ dot_part) {
-  __shared__ double red[256];
-  const int R2 = 2 * r - 1;
-  const int total = L * nband * Ns;  // per direction
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double dsum = 0.0;
-  if (idx < total) {
-    const int i = idx % Ns;
-    const int t = idx / Ns;
-    const int bp = t % nband, l = blockIdx.y * L + t / nband;  // flat (direction, slice)
-    int ny, nx;
-    band_pixel(bp, N, r, ny, nx);
-    const int cls = pix_class(ny, N, r) * R2 + pix_class(nx, N, r);
-    float2 corr = cmk(0.f, 0.f);
-    for (int j = 0; j < Ns; ++j) {
-      const float2* wc = wcls + (((size_t)l * R2 * R2 + cls) * Ns * Ns + i * Ns + j) * R2 * R2;
-      const float2* wp = wper + ((size_t)(l * Ns + i) * Ns + j) * R2 * R2;
-      const float2* xj = x + (size_t)(l * Ns + j) * N * N;
-      for (int dy = 0; dy < R2; ++dy) {
-        int yy = ny + dy - (r - 1);
-        bool iny = (yy >= 0 && yy < N);
-        int yw = yy < 0 ? yy + N : (yy >= N ? yy - N : yy);
-        for (int dx = 0; dx < R2; ++dx) {
-          int xx = nx + dx - (r - 1);
-          bool inx = (xx >= 0 && xx < N);
-          int xw = xx < 0 ? xx + N : (xx >= N ? xx - N : xx);
-          float2 v = xj[(size_t)yw * N + xw];
-          const int d = dy * R2 + dx;
-          float2 w = wp[d];
-          if (iny && inx) w = csub(w, wc[d]);
-          // corr -= (wper - wcls) v  on in-range taps, corr -= wper v on wrapped taps
-          corr.x -= w.x * v.x - w.y * v.y;
-          corr.y -= w.x * v.y + w.y * v.x;
+  extern __shared__ float2 bsm[];
+  __shared__ double red[8];
+  const int R2 = 2 * r - 1, w = r - 1;
+  const int strip = blockIdx.y;  // 0 top, 1 bottom, 2 left, 3 right
+  const int lf = blockIdx.z;     // flat (direction, slice)
+  const int d = lf / L, l = lf - d * L;
+  const int horiz = strip < 2;
+  const int lo = (strip == 0 || strip == 2);
+  const int nchunk = (N + BAND_TX - 1) / BAND_TX;
+  const int line = blockIdx.x / nchunk, chunk = blockIdx.x - line * nchunk;
+  const int tid = threadIdx.x, j = tid >> 5, lane = tid & 31;
+  const int nt = blockDim.x;
+  const int Wl = BAND_TX + R2 - 1;
+  const int start = (horiz ? 0 : w) + chunk * BAND_TX;
+  const int limit = horiz ? N : N - w;
+  const int fixed = (lo ? 0 : N - w) + line;
+  const size_t NN = (size_t)N * N;
+  const float2* xl = x + (size_t)lf * NS * NN;
+  const size_t cls_stride = (size_t)NS * R2 * R2 * NS;
+  const float2* dl = dcls + (size_t)lf * R2 * R2 * cls_stride;
+  float2* xs = bsm;                              // [NS][R2][Wl]
+  float2* part = xs + (size_t)NS * R2 * Wl;      // [NS (j)][BAND_TX][NS (i)]
+  const bool active = start < limit;
+  if (active) {
+    for (int e = tid; e < NS * R2 * Wl; e += nt) {
+      const int jj = e / (R2 * Wl), rem = e - jj * R2 * Wl;
+      const int aa = rem / Wl, u = rem - aa * Wl;
+      int gy, gx;
+      if (horiz) {
+        gy = fixed + aa - w;
+        gx = start - w + u;
+      } else {
+        gy = start - w + u;
+        gx = fixed + aa - w;
+      }
+      gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+      gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+      xs[e] = xl[(size_t)jj * NN + (size_t)gy * N + gx];
+    }
+  }
+  __syncthreads();
+  const int cfix = lo ? line : r + line;  // class along the fixed coordinate
+  if (active) {
+    const int clsline = horiz ? cfix * R2 + (r - 1) : (r - 1) * R2 + cfix;
+    const int pu0 = lane * BAND_P;
+    float2 acc[BAND_P][NS];
+#pragma unroll
+    for (int p = 0; p < BAND_P; ++p)
+#pragma unroll
+      for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
+    const float2* taps = dl + (size_t)clsline * cls_stride + (size_t)j * R2 * R2 * NS;
+    for (int aa = 0; aa < R2; ++aa) {
+      const float2* xr = xs + ((size_t)j * R2 + aa) * Wl + pu0;
+      for (int bb = 0; bb < R2; ++bb) {
+        const int dd = horiz ? aa * R2 + bb : bb * R2 + aa;
+        const float2* tp = taps + (size_t)dd * NS;
+        float2 tv[NS];
+        if (NS % 2 == 0) {
+#pragma unroll
+          for (int i = 0; i < NS; i += 2) {
+            const float4 t4 = __ldg(reinterpret_cast<const float4*>(tp + i));
+            tv[i] = cmk(t4.x, t4.y);
+            tv[i + 1 < NS ? i + 1 : i] = cmk(t4.z, t4.w);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < NS; ++i) tv[i] = __ldg(tp + i);
+        }
+#pragma unroll
+        for (int p = 0; p < BAND_P; ++p) {
+          const float2 xv = xr[p + bb];
+#pragma unroll
+          for (int i = 0; i < NS; ++i) cfma(acc[p][i], tv[i], xv);
         }
       }
     }
-    corr = cscale(corr, scale);
-    const size_t o = (size_t)(l * Ns + i) * N * N + (size_t)ny * N + nx;
-    out[o] = cadd(out[o], corr);
-    if (dot_part) {
-      float2 xv = x[o];
-      dsum = (double)xv.x * corr.x + (double)xv.y * corr.y;
+#pragma unroll
+    for (int p = 0; p < BAND_P; ++p) {
+      const int pos = start + pu0 + p;
+      if (horiz && pos < N && (pos < w || pos > N - r)) {
+        // corner pixel: its own class along x
+        const int cx = pos < w ? pos : (r - 1) + (pos - (N - r));
+        const float2* ct = dl + (size_t)(cfix * R2 + cx) * cls_stride + (size_t)j * R2 * R2 * NS;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
+        for (int aa = 0; aa < R2; ++aa)
+          for (int bb = 0; bb < R2; ++bb) {
+            const float2 xv = xs[((size_t)j * R2 + aa) * Wl + pu0 + p + bb];
+            const float2* tp = ct + (size_t)(aa * R2 + bb) * NS;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) cfma(acc[p][i], tp[i], xv);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < NS; ++i) part[((size_t)j * BAND_TX + pu0 + p) * NS + i] = acc[p][i];
+    }
+  }
+  __syncthreads();
+  double dsum = 0.0;
+  if (active) {
+    for (int t = tid; t < BAND_TX * NS; t += nt) {
+      const int pu = t / NS, i = t - pu * NS;
+      const int pos = start + pu;
+      if (pos >= limit) continue;
+      float2 sacc = part[(size_t)pu * NS + i];
+      for (int jj = 1; jj < NS; ++jj) sacc = cadd(sacc, part[((size_t)jj * BAND_TX + pu) * NS + i]);
+      const int ny = horiz ? fixed : pos, nx = horiz ? pos : fixed;
+      const size_t o = ((size_t)lf * NS + i) * NN + (size_t)ny * N + nx;
+      const float2 c = cscale(sacc, scale);
+      out[o] = cadd(out[o], c);
+      if (dot_part) {
+        const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
+        dsum += (double)xv.x * c.x + (double)xv.y * c.y;
+      }
     }
   }
   if (dot_part) {
-    red[threadIdx.x] = dsum;
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if (lane == 0) red[j] = dsum;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
+    if (tid == 0) {
+      double sacc = 0.0;
+      for (int k = 0; k < (nt >> 5); ++k) sacc += red[k];
+      dot_part[(size_t)d * SMSM_PART_MAX + ((size_t)l * 4 + strip) * gridDim.x + blockIdx.x] = sacc;
     }
-    if (threadIdx.x == 0) dot_part[(size_t)blockIdx.y * SMSM_PART_MAX + blockIdx.x] = red[0];
   }
 }
 
-int band_blocks(const smsm_plan_s* P) { return (P->L * P->nband * P->Ns + 255) / 256; }
+static int band_chunks(const smsm_plan_s* P) { return (P->r - 1) * ((P->N + BAND_TX - 1) / BAND_TX); }
+
+// partial sums per direction written by k_band
+int band_blocks(const smsm_plan_s* P) { return P->r > 1 ? P->L * 4 * band_chunks(P) : 0; }
+
+static size_t band_smem(const smsm_plan_s* P) {
+  const int R2 = P->R2;
+  return ((size_t)P->Ns * R2 * (BAND_TX + R2 - 1) + (size_t)P->Ns * BAND_TX * P->Ns) * sizeof(float2);
+}
+
+typedef void (*BandFn)(const float2*, float2*, const float2*, int, int, int, float, double*);
+static BandFn band_fn(const smsm_plan_s* P) {
+  switch (P->Ns) {
+    case 1: return k_band<1>;
+    case 2: return k_band<2>;
+    case 3: return k_band<3>;
+    case 4: return k_band<4>;
+    case 5: return k_band<5>;
+    case 6: return k_band<6>;
+    case 7: return k_band<7>;
+    default: return k_band<8>;
+  }
+}
+
+smsm_status band_init_attrs(const smsm_plan_s* P) {
+  cudaError_t e = cudaFuncSetAttribute(band_fn(P), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess || band_smem(P) > 200 * 1024) {
+    smsm_set_error("border-band kernel needs %zu bytes of shared memory", band_smem(P));
+    return SMSM_ERR_ARG;
+  }
+  return SMSM_OK;
+}
 
 smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, float scale, double* dot_part,
                         cudaStream_t s) {
-  const int nb = band_blocks(P);
-  if (nb <= 0) return SMSM_OK;
-  k_band<<<dim3(nb, P->D), 256, 0, s>>>(x, out, P->wper, P->wcls, P->L, P->Ns, P->N, P->r, P->nband, scale,
-                                        dot_part);
+  if (P->r <= 1) {  // filter 1: every patch is valid, the periodic value is exact
+    if (dot_part) SMSM_CUDA_TRY(cudaMemsetAsync(dot_part, 0, sizeof(double) * SMSM_PART_MAX * P->D, s));
+    return SMSM_OK;
+  }
+  dim3 grid(band_chunks(P), 4, P->LD);
+  band_fn(P)<<<grid, 32 * P->Ns, band_smem(P), s>>>(x, out, P->wcls, P->L, P->N, P->r, scale, dot_part);
   SMSM_LAUNCH_CHECK("k_band");
   return SMSM_OK;
 }

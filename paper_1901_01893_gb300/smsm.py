@@ -34,7 +34,8 @@ class Params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("eps0_rel", ctypes.c_double), ("eta", ctypes.c_double),
                 ("eps_min_rel", ctypes.c_double), ("outer_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("rank", ctypes.c_int), ("warm", ctypes.c_int),
-                ("max_sweeps", ctypes.c_int), ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("max_sweeps", ctypes.c_int), ("timing", ctypes.c_int), ("eig_cold", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class Report(ctypes.Structure):

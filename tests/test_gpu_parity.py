@@ -308,3 +308,21 @@ def test_fast_column_stage_matches_generic(smsm, L, Ns, Nc, N, r):
     if N <= 128:
         ref = O.reconstruct(y, S, r, dict(K=2, J=3, lam=3e-2))
         assert O.nrmse(out[0], ref) < 1e-4
+
+
+def test_warm_started_eigensolver_matches_cold(smsm):
+    # Jacobi started from the previous outer iteration's eigenvectors converges to
+    # the same eigen-decomposition as a cold start: same solve up to rounding.
+    key = "plain"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    g, xt, y = _problem(key, 4)
+    plan, _, _ = make_plan(smsm, key, sens=g["sens"])
+    out = []
+    for cold in (0, 1):
+        prm = smsm.default_params(lam=1e-2, outer_iters=4, cg_iters=4, eig_cold=cold)
+        x, rep = plan.reconstruct(c64(y), params=prm)
+        assert rep.status == 0
+        out.append((x.cpu().numpy(), [rep.sweeps[k] for k in range(4)]))
+    print("sweeps warm", out[0][1], "cold", out[1][1])
+    assert O.nrmse(out[0][0], out[1][0]) < 1e-4
+    assert sum(out[0][1][1:]) < sum(out[1][1][1:])  # warm starts need fewer sweeps
