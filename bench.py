@@ -47,6 +47,28 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def seed_for_rank(base_seed: int, rank: int) -> int:
+    """Replicas reconstruct different slice groups: rank r draws its inputs from base + 1000 r."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (timings: the job is as slow as its slowest replica)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, batch: int, ms_per_step: float) -> float:
+    """Whole-job slice groups per second: every rank finishes `batch` groups per step."""
+    return world * batch * 1000.0 / ms_per_step
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample, extrapolated to one reconstruction)
 # ---------------------------------------------------------------------------
@@ -231,7 +253,7 @@ def run_ours(args):
 
     cfg = dict(synth.CONFIGS[WORKLOAD])
     L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
-    seed = cfg["seed"] + 1000 * rank
+    seed = seed_for_rank(cfg["seed"], rank)
     D = args.batch
     c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(dev)  # noqa: E731
     plan = smsm.Plan(L, Ns, Nc, N, r, batch=D)
@@ -289,11 +311,8 @@ def run_ours(args):
         torch.distributed.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * D * 1000.0 / ms
+    ms = max_over_ranks(ms, dev)
+    value = throughput(world, D, ms)
 
     # end to end through the public API: pinned host y -> device, solve, x -> pinned host
     y_host = y.cpu().pin_memory()
@@ -310,10 +329,7 @@ def run_ours(args):
         e2e_ev[k][1].record()
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in e2e_ev) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
 
     if rank != 0:
         torch.distributed.destroy_process_group()
@@ -363,7 +379,7 @@ def run_ours(args):
                    "jacobi_sweeps_per_outer": [rep.sweeps[k] for k in range(cfg["K"])]},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * D * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
+        "e2e": {"value": throughput(world, D, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
                 "d2h_bytes_per_step": int(x.numel() * 8)},
         "gpu_launches": launches,
         "clocks": clocks,

@@ -21,6 +21,8 @@
 
 #include "common.cuh"
 
+#define CG_T 16  // tile edge of the small complex GEMMs (weights, warm-start congruence)
+
 __device__ __forceinline__ void jpair(int round, int k, int Cp, int& p, int& q) {
   const int m = Cp - 1;
   int a, b;
@@ -214,7 +216,6 @@ __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog,
 
 // Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
 // step 0: T = G V (G in FP64, rounded on load); step 1: Gw = V^H T.
-#define CG_T 16
 __global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ G, const float2* __restrict__ V,
                                                     const float2* __restrict__ Tin, float2* __restrict__ out, int C,
                                                     int step) {
@@ -284,15 +285,17 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
   }
 }
 
-// W[a][b] = sum_j V[a][j] f_j conj(V[b][j])
+// W[a][b] = sum_j V[a][j] f_j conj(V[b][j]), f_j = (max(s_j, 0) + eps)^(-1/2) (IRLS) or
+// [s_j among the C - rank smallest] (NULLSPACE).  16 x 16 output tiles, K tiles of 16.
 __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, const float* __restrict__ eig,
                                                  const SolverState* __restrict__ st, float2* __restrict__ W, int C,
                                                  int Cp, int mode, int rank, int L) {
   __shared__ float f[SMSM_MAX_C];
-  __shared__ float2 Va[16][SMSM_MAX_C];
-  const int l = blockIdx.x, a0 = blockIdx.y * 16;
+  __shared__ float2 As[CG_T][CG_T + 1];
+  __shared__ float2 Bs[CG_T][CG_T + 1];
+  const int l = blockIdx.z;  // flat (direction, slice)
   const float* s = eig + (size_t)l * Cp;
-  const double eps = st[l / L].eps;  // l is the flat (direction, slice) index
+  const double eps = st[l / L].eps;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     if (mode == SMSM_MODE_NULLSPACE) {
       int rk = 0;
@@ -303,27 +306,22 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
       f[j] = (float)(1.0 / sqrt(fmax((double)s[j], 0.0) + eps));
     }
   }
-  const float2* Vl = V + (size_t)l * C * C;
-  for (int e = threadIdx.x; e < 16 * C; e += blockDim.x) {
-    int ar = e / C, j = e - ar * C;
-    Va[ar][j] = (a0 + ar < C) ? Vl[(size_t)(a0 + ar) * C + j] : cmk(0.f, 0.f);
-  }
   __syncthreads();
-  const int ar = threadIdx.x >> 4;
-  const int a = a0 + ar;
-  if (a >= C) return;
-  for (int b = threadIdx.x & 15; b < C; b += 16) {
-    const float2* Vb = Vl + (size_t)b * C;
-    float2 acc = cmk(0.f, 0.f);
-    for (int j = 0; j < C; ++j) {
-      float2 va = cscale(Va[ar][j], f[j]);
-      float2 vb = Vb[j];
-      // va * conj(vb)
-      acc.x += va.x * vb.x + va.y * vb.y;
-      acc.y += va.y * vb.x - va.x * vb.y;
-    }
-    W[((size_t)l * C + a) * C + b] = acc;
+  const float2* Vl = V + (size_t)l * C * C;
+  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
+  const int a0 = blockIdx.y * CG_T, b0 = blockIdx.x * CG_T;
+  float2 acc = cmk(0.f, 0.f);
+  for (int k0 = 0; k0 < C; k0 += CG_T) {
+    const int ka = k0 + tx;
+    // As[row a][k] = V[a][k] f_k ; Bs[k][col b] = conj(V[b][k])  (loads coalesced along k)
+    As[ty][tx] = (a0 + ty < C && ka < C) ? cscale(Vl[(size_t)(a0 + ty) * C + ka], f[ka]) : cmk(0.f, 0.f);
+    Bs[tx][ty] = (b0 + ty < C && ka < C) ? conjf2(Vl[(size_t)(b0 + ty) * C + ka]) : cmk(0.f, 0.f);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
+    __syncthreads();
   }
+  if (a0 + ty < C && b0 + tx < C) W[((size_t)l * C + a0 + ty) * C + b0 + tx] = acc;
 }
 
 static size_t jacobi_smem(int Cp) {
@@ -372,8 +370,8 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, C, Cp, outer, prm->eps0_rel, prm->eta,
                              prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
-  dim3 gw(P->LD, (C + 15) / 16);
-  k_weights<<<gw, 256, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
+  dim3 gw((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
+  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
   SMSM_LAUNCH_CHECK("k_weights");
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;

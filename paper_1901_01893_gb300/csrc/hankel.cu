@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, floa
     const float2* taps = dl + (size_t)clsline * cls_stride + (size_t)j * R2 * R2 * NS;
     for (int aa = 0; aa < R2; ++aa) {
       const float2* xr = xs + ((size_t)j * R2 + aa) * Wl + pu0;
+#pragma unroll 4
       for (int bb = 0; bb < R2; ++bb) {
         const int dd = horiz ? aa * R2 + bb : bb * R2 + aa;
         const float2* tp = taps + (size_t)dd * NS;
