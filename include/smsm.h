@@ -66,8 +66,18 @@ typedef struct {
   int caipi_div;   /* CAIPI FOV shift is FOV/caipi_div per slice index; 0 -> mb (Eq. 1) */
   int batch;       /* D, number of problems per call; 0 -> 1 (at most 4096) */
   int flags;       /* SMSM_FLAG_* bits */
-  int reserved[5];
+  int precision;   /* smsm_precision of the Hankel Gram (default FP32) */
+  int reserved[4];
 } smsm_opts;
+
+/*
+ * Precision of the Hankel Gram, which runs on the tensor cores when C <= 144
+ * (larger C: FP32 FMA; the BF16 split form needs C <= 144):
+ *   FP32: every value split as x = hi + lo with hi a TF32 value, three TF32
+ *         products hi*hi + hi*lo + lo*hi, FP32 accumulation (FP32-accurate);
+ *   BF16_SPLIT: the same with BF16 hi and lo (~2^-16 relative per product).
+ */
+typedef enum { SMSM_PRECISION_FP32 = 0, SMSM_PRECISION_BF16_SPLIT = 1 } smsm_precision;
 
 /* smsm_opts.flags: use the shape-generic kernels even where a specialised fast
  * path exists (same results up to rounding; for testing and comparison). */
@@ -231,6 +241,13 @@ smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, i
  */
 smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, int n, int filter,
                                      void* stream);
+
+/*
+ * Synchronise `stream` and report the plan's device error flag: SMSM_OK, or
+ * SMSM_ERR_TIMEOUT when a kernel gave up a bounded wait (its outputs are then
+ * unspecified).  smsm_reconstruct's report carries the same flag.
+ */
+smsm_status smsm_plan_device_status(smsm_plan_t plan, void* stream);
 
 /* Message of the calling thread's last failed call ("" if none). */
 const char* smsm_last_error(void);

@@ -95,7 +95,8 @@ static void free_plan(smsm_plan_s* P) {
   void* ptrs[] = {P->twN,  P->twM,  P->tw_shot, P->cph,  P->Etab,  P->sensT, P->hA,   P->hB,
                   P->yh,   P->phaseT, P->xs,    P->bv,   P->rv,    P->pv,    P->qv,   P->ybuf,
                   P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2,
-                  P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep};
+                  P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep,
+                  P->Rpart, P->devflag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->has_graph) cudaGraphExecDestroy(P->gexec);
@@ -164,6 +165,19 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   P->D = D;
   P->LD = D * mb;
   P->flags = opts ? opts->flags : 0;
+  P->precision = opts ? opts->precision : SMSM_PRECISION_FP32;
+  if (P->precision != SMSM_PRECISION_FP32 && P->precision != SMSM_PRECISION_BF16_SPLIT) {
+    free(P);
+    smsm_set_error("smsm_plan: unknown precision %d", opts->precision);
+    return SMSM_ERR_ARG;
+  }
+  P->gram_tc = gram_tc_supported(P) && !(P->flags & SMSM_FLAG_GENERIC_KERNELS);
+  if (P->precision == SMSM_PRECISION_BF16_SPLIT && !gram_tc_supported(P)) {
+    free(P);
+    smsm_set_error("smsm_plan: the BF16 split form needs C = shots*filter^2 <= 144");
+    return SMSM_ERR_ARG;
+  }
+  if (P->precision == SMSM_PRECISION_BF16_SPLIT) P->gram_tc = 1;
   P->P1 = N - r + 1;
   P->R2 = 2 * r - 1;
   P->fN = fN;
@@ -214,6 +228,12 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(part_pq_band, (size_t)D * SMSM_PART_MAX);
   A(part_rr, (size_t)2 * D * SMSM_PART_MAX);
   A(st, D);
+  if (P->gram_tc) {
+    P->gram_tc_nG = gram_tc_nG(P);
+    const size_t R2C = 2 * (size_t)gram_tc_cp(P);
+    A(Rpart, LD * P->gram_tc_nG * R2C * R2C);
+  }
+  A(devflag, 1);
   A(rep, 1);
 #undef A
   if (st) {
@@ -269,6 +289,14 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   if (!st) st = operators_init_attrs();
   if (!st) st = colfast_init_attrs();
   if (!st) st = band_init_attrs(P);
+  if (!st) st = gram_tc_init_attrs();
+  if (!st) {
+    cudaError_t e = cudaMemset(P->devflag, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      smsm_set_error("smsm_plan: %s", cudaGetErrorString(e));
+      st = SMSM_ERR_CUDA;
+    }
+  }
   if (!st) st = eig_init_attrs(Cp);
   if (!st && smsm_col_smem_bytes(P) > 200 * 1024) {
     smsm_set_error("smsm_plan: column stage would need %zu bytes of shared memory", smsm_col_smem_bytes(P));
@@ -428,6 +456,18 @@ extern "C" smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, i
     float2* dst = (float2*)out + (size_t)b0 * NN;
     if ((st = launch_rowfft_out_T(plan, src, plan->hA, nb, plan->N, inverse != 0, s))) return st;
     if ((st = launch_rowfft_out_T(plan, plan->hA, dst, nb, plan->N, inverse != 0, s))) return st;
+  }
+  return SMSM_OK;
+}
+
+extern "C" smsm_status smsm_plan_device_status(smsm_plan_t plan, void* stream) {
+  CHECK_PLAN("smsm_plan_device_status");
+  int flag = 0;
+  SMSM_CUDA_TRY(cudaMemcpyAsync(&flag, plan->devflag, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+  SMSM_CUDA_TRY(cudaStreamSynchronize(S(stream)));
+  if (flag) {
+    smsm_set_error("a kernel gave up a bounded wait (device status %d)", flag);
+    return (smsm_status)flag;
   }
   return SMSM_OK;
 }

@@ -75,7 +75,12 @@ struct DevReport {
 struct smsm_plan_s {
   int L, Ns, Nc, N, r, C, Cp /* C rounded up to even */, M, Ldiv, P1 /* N-r+1 */, R2 /* 2r-1 */;
   int D;   // batch: independent problems (diffusion directions) sharing geometry and coil maps
-  int flags;  // smsm_opts.flags
+  int flags;      // smsm_opts.flags
+  int precision;  // smsm_opts.precision
+  int gram_tc;    // 1: tensor-core Gram
+  int gram_tc_nG; // split-K partials of the tensor-core Gram
+  float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials
+  int* devflag;   // device error flag raised by bounded waits (SMSM_ERR_TIMEOUT)
   int LD;  // D * L: number of (direction, slice) Hankel matrices
   int nband;  // pixels within r-1 of an edge
   int dev;
@@ -217,6 +222,12 @@ smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const flo
                        cudaStream_t s);
 // hankel.cu
 smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
+// gram_tc.cu
+int gram_tc_supported(const smsm_plan_s* P);
+int gram_tc_cp(const smsm_plan_s* P);
+int gram_tc_nG(const smsm_plan_s* P);
+smsm_status gram_tc_init_attrs();
+smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s);
 smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, float scale, double* dot_part,
                         cudaStream_t s);

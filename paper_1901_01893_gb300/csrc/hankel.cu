@@ -128,6 +128,7 @@ __global__ void k_gram_reduce(const double2* __restrict__ part, double2* __restr
 }
 
 smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s) {
+  if (P->gram_tc) return launch_gram_tc(P, x, G, s);
   const int tside = (P->C + GT - 1) / GT;
   const int ntile = tside * (tside + 1) / 2;
   const int nkx = P->gram_nkx;

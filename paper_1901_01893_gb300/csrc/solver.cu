@@ -330,6 +330,9 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
     SMSM_CUDA_TRY(cudaStreamSynchronize(s));
     memset(report, 0, sizeof(*report));
     for (int d = 0; d < P->D && !report->status; ++d) report->status = hs[d].status;
+    int flag = 0;
+    SMSM_CUDA_TRY(cudaMemcpy(&flag, P->devflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!report->status && flag) report->status = flag;
     report->outer_done = prm->outer_iters;
     const int K = prm->outer_iters < SMSM_MAX_OUTER ? prm->outer_iters : SMSM_MAX_OUTER;
     for (int k = 0; k < K; ++k) {

@@ -19,6 +19,7 @@ SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
 SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_FLAG_GENERIC_KERNELS = 1
+SMSM_PRECISION_FP32, SMSM_PRECISION_BF16_SPLIT = 0, 1
 SMSM_MAX_OUTER = 128
 STAGES = ["adjoint", "gram", "eig", "vapply", "weights", "filters", "rowfft_inv", "column", "rowfft_fwd",
           "band", "cg"]
@@ -27,7 +28,7 @@ STAGE = {name: k for k, name in enumerate(STAGES)}
 
 class Opts(ctypes.Structure):
     _fields_ = [("caipi_div", ctypes.c_int), ("batch", ctypes.c_int), ("flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Params(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib() -> ctypes.CDLL:
     L.smsm_fft2c.restype = st
     L.smsm_hankel_gram_noalloc.argtypes = [vp, vp, i, i, i, i, vp]
     L.smsm_hankel_gram_noalloc.restype = st
+    L.smsm_plan_device_status.argtypes = [vp, vp]
+    L.smsm_plan_device_status.restype = st
     L.smsm_last_error.argtypes = []
     L.smsm_last_error.restype = ctypes.c_char_p
     L.smsm_default_params.argtypes = [ctypes.POINTER(Params)]
@@ -140,13 +143,13 @@ class Plan:
     """
 
     def __init__(self, mb: int, shots: int, coils: int, n: int, filter: int, caipi_div: int = 0,
-                 batch: int = 1, flags: int = 0):
+                 batch: int = 1, flags: int = 0, precision: int = 0):
         self.L, self.Ns, self.Nc, self.N, self.r = mb, shots, coils, n, filter
         self.D = batch
         self.C = shots * filter * filter
         self.M = n // shots if shots else 0
         h = ctypes.c_void_p()
-        opts = Opts(caipi_div=caipi_div, batch=batch, flags=flags)
+        opts = Opts(caipi_div=caipi_div, batch=batch, flags=flags, precision=precision)
         _check(lib().smsm_plan(ctypes.byref(h), mb, shots, coils, n, n, filter, ctypes.byref(opts)))
         self._h = h
 
@@ -160,6 +163,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def device_status(self) -> int:
+        """Synchronise and return the plan's device error flag (0 = fine)."""
+        return lib().smsm_plan_device_status(self._h, _stream())
 
     @property
     def workspace_bytes(self) -> int:

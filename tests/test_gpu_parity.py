@@ -326,3 +326,42 @@ def test_warm_started_eigensolver_matches_cold(smsm):
     print("sweeps warm", out[0][1], "cold", out[1][1])
     assert O.nrmse(out[0][0], out[1][0]) < 1e-4
     assert sum(out[0][1][1:]) < sum(out[1][1][1:])  # warm starts need fewer sweeps
+
+
+@pytest.mark.parametrize("key", ["tiny", "plain", "radix3", "mb3_8shots"])
+def test_tensor_core_gram_matches_fma_gram(smsm, key):
+    # tcgen05 Gram (TF32 split, FP32-accurate) against the FP32-FMA Gram and the oracle
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    rng = np.random.default_rng(31)
+    x = crandn(rng, L, Ns, N, N).astype(np.complex64)
+    ref = O.gram(x.astype(np.complex128), r)
+    out = {}
+    for flags in (0, smsm.SMSM_FLAG_GENERIC_KERNELS):
+        p = smsm.Plan(L, Ns, Nc, N, r, flags=flags)
+        out[flags] = p.hankel_gram(c64(x)).cpu().numpy()
+        assert p.device_status() == 0
+    assert O.nrmse(out[0], ref) < OP_TOL
+    assert O.nrmse(out[0], out[smsm.SMSM_FLAG_GENERIC_KERNELS]) < OP_TOL
+
+
+def test_bf16_split_precision_form(smsm):
+    # the BF16 split Gram (3 BF16 products, FP32 accumulate): error per slice reported,
+    # below the 1e-3 metric threshold for the Gram and for the whole solve
+    key = "plain"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    rng = np.random.default_rng(32)
+    x = crandn(rng, L, Ns, N, N).astype(np.complex64)
+    p = smsm.Plan(L, Ns, Nc, N, r, precision=smsm.SMSM_PRECISION_BF16_SPLIT)
+    G = p.hankel_gram(c64(x)).cpu().numpy()
+    ref = O.gram(x.astype(np.complex128), r)
+    per_slice = [O.nrmse(G[l], ref[l]) for l in range(L)]
+    print("BF16 split Gram NRMSE per slice", per_slice)
+    assert max(per_slice) < 1e-4
+    g, xt, y = _problem(key, 6)
+    ref = O.reconstruct(y, g["sens"], r, dict(K=3, J=4, lam=1e-2), Ldiv=Ldiv)
+    p.set_sens(c64(g["sens"]))
+    xr, rep = p.reconstruct(c64(y), params=smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4))
+    assert rep.status == 0
+    err = O.nrmse(xr.cpu().numpy(), ref)
+    print("BF16 split solve NRMSE vs FP64 oracle", err)
+    assert err < SOLVE_TOL
