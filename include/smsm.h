@@ -191,7 +191,8 @@ smsm_status smsm_adjoint(smsm_plan_t plan, const void* y, const void* phase, voi
  * G_l = H_l^H H_l for every slice (Eqs. 8-9): x is [L][Ns][N][N] complex64,
  * G is [L][C][C] complex128 (full Hermitian matrix, overwritten), with
  * G[(i,p),(i',q)] = sum_{k in [0,N-r]^2} conj(x_i[k+p]) x_i'[k+q],
- * column index (i,p) = i*r*r + py*r + px.
+ * column index (i,p) = i*r*r + py*r + px.  x must be 16-byte aligned (its image
+ * rows are copied into shared memory by bulk copies); SMSM_ERR_ARG otherwise.
  */
 smsm_status smsm_hankel_gram(smsm_plan_t plan, const void* x, void* G, void* stream);
 

@@ -415,6 +415,10 @@ extern "C" smsm_status smsm_hankel_gram(smsm_plan_t plan, const void* x, void* G
   CHECK_PLAN("smsm_hankel_gram");
   CHECK_PTR("smsm_hankel_gram", x);
   CHECK_PTR("smsm_hankel_gram", G);
+  if ((uintptr_t)x & 15u) {
+    smsm_set_error("smsm_hankel_gram: x must be 16-byte aligned");
+    return SMSM_ERR_ARG;
+  }
   return launch_gram(plan, (const float2*)x, (double2*)G, S(stream));
 }
 

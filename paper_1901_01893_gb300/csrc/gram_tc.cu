@@ -6,38 +6,39 @@
 // [0, Cp), Im in [Cp, 2Cp).
 //
 // One CTA computes a 128-row tile t of R against all 2Cp columns (two MMAs of
-// N = Cp) over a strided subset of the patch chunks (split-K); its FP32
-// partial goes to global memory and k_gram_tc_reduce adds the partials in FP64
-// in a fixed order.  Per chunk of 16 patches, the 128 threads gather the Hankel
-// entries x_i[k+p] straight from the image (implicit im2col), split every value
-// into hi + lo and write X^T (all 2Cp rows, hi and lo) into one of two
-// shared-memory stages in the canonical K-major layout; one thread then issues
-// the MMAs  D += Xh_t Xh^T + Xh_t Xl^T + Xl_t Xh^T  (the A tile is a row window
-// of the same staged X^T) and commits them to the stage's mbarrier, so staging
-// the next chunk overlaps the tensor-core work.  The accumulator (128 lanes x
-// 2Cp FP32 columns) stays in TMEM until the epilogue reads it back.
+// N = Cp) over a contiguous block of patch rows ky (split-K); its FP32 partial
+// goes to global memory and k_gram_tc_reduce adds the partials in FP64 in a
+// fixed order.  Roles (warp-specialised, 288 threads):
+//   * thread 0 brings the window of patch row ky -- image rows ky..ky+r-1 of
+//     every shot -- into shared memory with TMA bulk copies (two windows in
+//     flight, completion counted on an mbarrier);
+//   * warps 0-3 build each chunk of KCH patches (32 bytes along K) from the
+//     window (implicit im2col), split every value into hi + lo and write X^T
+//     (all 2Cp rows, hi and lo) into a 3-stage ring in the canonical K-major
+//     layout;
+//   * one thread of warp 8 issues  D += Xh_t Xh^T + Xh_t Xl^T + Xl_t Xh^T
+//     (the A tile is a row window of the same staged X^T) and commits each
+//     stage back to its producers;
+//   * warps 4-7 drain the TMEM accumulator every GTC_EPOCH chunks into the
+//     CTA's FP32 partial in global memory (each thread owns one row and adds
+//     with fire-and-forget reductions), which bounds the error
+//     that the tensor core's FP32 accumulation gathers over many chunks.
 //   precision 0: TF32 split (hi = x with the low 13 mantissa bits cleared,
 //                lo = x - hi): products accurate to ~2^-21, like FP32 FMA.
 //   precision 1: BF16 split (hi = bf16(x), lo = bf16(x - hi)): ~2^-16.
 // Every wait on an mbarrier is bounded; on a timeout the kernel raises the
-// plan's device error flag, waits (bounded) for its last MMAs, frees TMEM and
-// returns.
+// plan's device error flag, lets its in-flight bulk copies and MMAs finish
+// (bounded waits), frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "umma.cuh"
 
-#define GTC_THREADS 288   // warps 0-3: producers; warps 4-7: accumulator drain; warp 8 lane 0: MMA issue
-#define GTC_STAGES 3      // shared-memory ring of staged chunks
-#define GTC_EPOCH 32      // chunks accumulated in TMEM before draining into the FP32 running sum
+#define GTC_PROD_WARPS 6                               // im2col producers
+#define GTC_THREADS (32 * (GTC_PROD_WARPS + 4 + 1))     // + 4 drain warps + 1 MMA warp
+#define GTC_KSTEP 2                                    // MMA k-steps (32 bytes of K each) per staged chunk
+#define GTC_EPOCH 16                                   // chunks accumulated in TMEM before a drain
 #define GTC_MAXITER (1L << 22)
-
-// patches per chunk: one MMA (32 bytes along K) per chunk and pass
-template <int PREC>
-struct GtcCfg {
-  static constexpr int ESZ = PREC == 0 ? 4 : 2;
-  static constexpr int KCH = 32 / ESZ;
-};
 
 // bounded wait that also gives up when another role has aborted
 __device__ __forceinline__ bool gtc_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag) {
@@ -54,54 +55,82 @@ __device__ __forceinline__ bool gtc_wait(uint64_t* mbar, uint32_t parity, volati
   return false;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)));
+// shared-memory layout of one CTA (bytes); the same function sizes the launch
+struct GtcLayout {
+  int rows_alloc;    // 128 * number of row tiles
+  int wp;            // window row pitch (complex elements): N + 8, shifts consecutive rows by 8 banks
+  size_t arr_bytes;  // one of hi / lo of one staged chunk: rows_alloc x (32 GTC_KSTEP) bytes
+  size_t win_elems;  // one window: Ns*r rows of wp elements
+  int nst;           // ring stages (3, or 2 when three do not fit)
+  size_t total;
+};
+
+__host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp) {
+  GtcLayout L;
+  L.rows_alloc = 128 * ((2 * Cp + 127) / 128);
+  L.wp = N + 8;
+  L.arr_bytes = (size_t)L.rows_alloc * 32 * GTC_KSTEP;
+  L.win_elems = (size_t)Ns * r * L.wp;
+  const size_t win = 2 * L.win_elems * 8;
+  L.nst = (2 * 3 * L.arr_bytes + win <= (size_t)224 * 1024) ? 3 : 2;
+  L.total = 2 * L.nst * L.arr_bytes + win;
+  return L;
 }
 
+// This CTA: row tile t of R, patch rows ky in [ky0, ky1) (block g of nG), matrix lf.
+// A chunk is KCH = 32 GTC_KSTEP / ESZ consecutive patches of one patch row (the row's
+// tail zero-padded).  Producer unit = one 16-byte core-matrix row: column c of X (its
+// Re and Im rows of X^T), EPC consecutive patches.
 template <int PREC>
 __global__ void __launch_bounds__(GTC_THREADS, 1)
     k_gram_tc(const float2* __restrict__ x, float* __restrict__ Rpart, int* __restrict__ errflag, int Ns, int N,
               int r, int C, int Cp, int nG) {
-  constexpr int ESZ = GtcCfg<PREC>::ESZ;        // bytes per operand element
-  constexpr int KCH = GtcCfg<PREC>::KCH;        // patches per chunk (32 bytes along K)
-  constexpr int EPC = 16 / ESZ;                 // elements per 16-byte core-matrix row
-  constexpr uint32_t LBO = 128;                 // next core matrix along K
-  constexpr uint32_t SBO = 256;                 // next 8-row group (2 core matrices along K)
-  constexpr int NPROD = 128;                    // producer threads
+  constexpr int ESZ = PREC == 0 ? 4 : 2;         // bytes per operand element
+  constexpr int EPC = 16 / ESZ;                  // elements per 16-byte core-matrix row
+  constexpr int KQ = 2 * GTC_KSTEP;              // core matrices along K per chunk
+  constexpr int KCH = KQ * EPC;                  // patches per chunk
+  constexpr uint32_t LBO = 128;                  // next core matrix along K
+  constexpr uint32_t SBO = 128 * KQ;             // next 8-row group
+  constexpr int NPROD = 32 * GTC_PROD_WARPS;     // producer threads
   extern __shared__ __align__(1024) unsigned char gsm[];
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t full_b[GTC_STAGES], empty_b[GTC_STAGES], accfull_b, accempty_b;
+  __shared__ __align__(8) uint64_t full_b[3], empty_b[3], accfull_b, accempty_b, win_b[2], fin_b;
   __shared__ volatile int s_abort;
 
   const int t = blockIdx.x, g = blockIdx.y, lf = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R2C = 2 * Cp;
-  const int ntile = (R2C + 127) / 128;
-  const int rows_alloc = ntile * 128;
-  const size_t arr_bytes = (size_t)rows_alloc * 32;  // one of hi / lo, one chunk
-  float* Ssum = reinterpret_cast<float*>(gsm + 2 * GTC_STAGES * arr_bytes);  // [128][R2C + 1] running sum
-  const int sld = R2C + 1;
-  const int P1 = N - r + 1, P = P1 * P1;
-  const int nchunks = (P + KCH - 1) / KCH;
+  const GtcLayout Lo = gtc_layout(Ns, N, r, Cp);
+  const int NST = Lo.nst;
+  const size_t arr_bytes = Lo.arr_bytes;
+  const int WP = Lo.wp;
+  float2* win = reinterpret_cast<float2*>(gsm + 2 * NST * arr_bytes);  // [2][Ns*r][WP]
+  const int P1 = N - r + 1;
+  const int ky0 = (int)((long)g * P1 / nG), ky1 = (int)((long)(g + 1) * P1 / nG);
+  const int nchx = (P1 + KCH - 1) / KCH;
+  const int nit = (ky1 - ky0) * nchx;
+  const int nepoch = (nit + GTC_EPOCH - 1) / GTC_EPOCH;
   const int rr = r * r;
   const size_t NN = (size_t)N * N;
   const float2* xl = x + (size_t)lf * Ns * NN;
   const bool need_h0 = Cp > 128 * t;  // columns [0, Cp) reach the upper triangle of this row tile
   const int c_begin = need_h0 ? 0 : Cp;
-  const int nit = nchunks > g ? (nchunks - g + nG - 1) / nG : 0;
-  const int nepoch = (nit + GTC_EPOCH - 1) / GTC_EPOCH;
+  const uint32_t win_bytes = (uint32_t)((size_t)Ns * r * N * sizeof(float2));
+  const int tmem_cols = R2C > 256 ? 512 : 256;
 
-  for (size_t e = tid; e < 2 * GTC_STAGES * arr_bytes / 16; e += GTC_THREADS)
+  for (size_t e = tid; e < 2 * NST * arr_bytes / 16; e += GTC_THREADS)
     reinterpret_cast<uint4*>(gsm)[e] = make_uint4(0, 0, 0, 0);
-  for (int e = tid; e < 128 * sld; e += GTC_THREADS) Ssum[e] = 0.f;
-  if (warp == 0) tmem_alloc(&tmem_base, R2C > 256 ? 512 : 256);
+  if (warp == 0) tmem_alloc(&tmem_base, tmem_cols);
   if (tid == 0) {
-    for (int k = 0; k < GTC_STAGES; ++k) {
+    for (int k = 0; k < NST; ++k) {
       mbar_init(&full_b[k], NPROD);
       mbar_init(&empty_b[k], 1);
     }
     mbar_init(&accfull_b, 1);
     mbar_init(&accempty_b, 128);
+    mbar_init(&win_b[0], 1);
+    mbar_init(&win_b[1], 1);
+    mbar_init(&fin_b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_abort = 0;
   }
@@ -110,139 +139,197 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  if (warp < 4) {
-    // ---------------- producers: implicit im2col into the ring ----------------
-    constexpr int IPT = (144 * KCH + NPROD - 1) / NPROD;  // Cp <= 144
-    int kk[IPT];
-    long coff[IPT];
-    uint32_t ore[IPT], oim[IPT];
+  // window ky -> buffer b: image rows ky..ky+r-1 of every shot, one TMA bulk copy per row
+  auto load_window = [&](int ky, int b) {
+    fence_async_smem();
+    mbar_arrive_expect_tx(&win_b[b], win_bytes);
+    for (int ip = 0; ip < Ns * r; ++ip) {
+      const int i = ip / r, py = ip - i * r;
+      tma_bulk_g2s(win + (size_t)b * Lo.win_elems + (size_t)ip * WP, xl + (size_t)i * NN + (size_t)(ky + py) * N,
+                   (uint32_t)(N * sizeof(float2)), &win_b[b]);
+    }
+  };
+
+  if (warp < GTC_PROD_WARPS) {
+    // ---------------- producers: im2col from the staged windows into the ring ----------------
+    constexpr int UPT = (144 * KQ + NPROD - 1) / NPROD;  // Cp <= 144
+    int woff[UPT], kofs[UPT];
+    uint32_t ore[UPT], oim[UPT];
+    bool act[UPT];
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const int e = tid + NPROD * j;
-      kk[j] = -1;
-      coff[j] = -1;
+    for (int j = 0; j < UPT; ++j) {
+      const int u = tid + NPROD * j;
+      act[j] = u < Cp * KQ;
+      woff[j] = -1;
+      kofs[j] = 0;
       ore[j] = oim[j] = 0;
-      if (e < Cp * KCH) {
-        const int r8 = e & 7;
-        const int kin = (e >> 3) % EPC;
-        const int kq = (e / (8 * EPC)) % (KCH / EPC);
-        const int cg = e / (8 * KCH);
+      if (act[j]) {
+        const int r8 = u & 7, kq = (u >> 3) % KQ, cg = u / (8 * KQ);
         const int c = cg * 8 + r8;
-        kk[j] = kq * EPC + kin;
-        ore[j] = umma_kmajor_off(c, kk[j] * ESZ, LBO, SBO);
-        oim[j] = umma_kmajor_off(Cp + c, kk[j] * ESZ, LBO, SBO);
+        kofs[j] = kq * EPC;
+        ore[j] = umma_kmajor_off(c, kq * 16, LBO, SBO);
+        oim[j] = umma_kmajor_off(Cp + c, kq * 16, LBO, SBO);
         if (c < C) {
           const int i = c / rr, p = c - i * rr;
           const int py = p / r, px = p - py * r;
-          coff[j] = (long)i * (long)NN + (long)py * N + px;
+          woff[j] = (i * r + py) * WP + px + kq * EPC;
         }
       }
     }
-    auto gather = [&](int chunk, float2 (&vv)[IPT]) {
-      const int q0 = chunk * KCH;
-      const int ky0 = q0 / P1, kx0 = q0 - ky0 * P1;
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        vv[j] = cmk(0.f, 0.f);
-        if (coff[j] >= 0) {
-          int kx = kx0 + kk[j], ky = ky0;
-          if (kx >= P1) {
-            kx -= P1;
-            ++ky;
+    // Thread 0 keeps two windows in flight; window w (patch row ky0 + w) goes to buffer w & 1.
+    // Every producer ends each patch row at a reducing barrier, so all of them take the
+    // same decision to go on or to stop, and none is left waiting at a barrier.
+    int issued = 0, consumed = 0;
+    if (tid == 0)
+      for (; issued < 2 && ky0 + issued < ky1; ++issued) load_window(ky0 + issued, issued);
+    int it = 0;
+    for (int ky = ky0; ky < ky1; ++ky) {
+      const int w = ky - ky0, wb = w & 1;
+      bool mine = gtc_wait(&win_b[wb], (uint32_t)((w >> 1) & 1), &s_abort);
+      if (mine) {
+        const float2* W = win + (size_t)wb * Lo.win_elems;
+        for (int cx = 0; cx < nchx; ++cx, ++it) {
+          const int s = it % NST;
+          if (it >= NST && !gtc_wait(&empty_b[s], (uint32_t)((it / NST - 1) & 1), &s_abort)) {
+            mine = false;
+            break;
           }
-          if (q0 + kk[j] < P) vv[j] = __ldg(xl + coff[j] + (size_t)ky * N + kx);
-        }
-      }
-    };
-    float2 v[IPT];
-    if (nit > 0) gather(g, v);
-    for (int it = 0; it < nit; ++it) {
-      const int s = it % GTC_STAGES;
-      if (it >= GTC_STAGES && !gtc_wait(&empty_b[s], (uint32_t)((it / GTC_STAGES - 1) & 1), &s_abort)) break;
-      unsigned char* hi = gsm + (size_t)s * 2 * arr_bytes;
-      unsigned char* lo = hi + arr_bytes;
+          unsigned char* hi = gsm + (size_t)s * 2 * arr_bytes;
+          unsigned char* lo = hi + arr_bytes;
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        if (kk[j] < 0) continue;
-        if (PREC == 0) {
-          const float hre = __uint_as_float(__float_as_uint(v[j].x) & 0xFFFFE000u);
-          const float him = __uint_as_float(__float_as_uint(v[j].y) & 0xFFFFE000u);
-          *reinterpret_cast<float*>(hi + ore[j]) = hre;
-          *reinterpret_cast<float*>(hi + oim[j]) = him;
-          *reinterpret_cast<float*>(lo + ore[j]) = v[j].x - hre;
-          *reinterpret_cast<float*>(lo + oim[j]) = v[j].y - him;
-        } else {
-          const __nv_bfloat16 hre = __float2bfloat16_rn(v[j].x), him = __float2bfloat16_rn(v[j].y);
-          *reinterpret_cast<__nv_bfloat16*>(hi + ore[j]) = hre;
-          *reinterpret_cast<__nv_bfloat16*>(hi + oim[j]) = him;
-          *reinterpret_cast<__nv_bfloat16*>(lo + ore[j]) = __float2bfloat16_rn(v[j].x - __bfloat162float(hre));
-          *reinterpret_cast<__nv_bfloat16*>(lo + oim[j]) = __float2bfloat16_rn(v[j].y - __bfloat162float(him));
+          for (int j = 0; j < UPT; ++j) {
+            if (!act[j]) continue;
+            const int kx0 = cx * KCH + kofs[j];  // first patch of this unit
+            float re[EPC], im[EPC];
+#pragma unroll
+            for (int m = 0; m < EPC; ++m) {
+              float2 v = cmk(0.f, 0.f);
+              if (woff[j] >= 0 && kx0 + m < P1) v = W[woff[j] + cx * KCH + m];
+              re[m] = v.x;
+              im[m] = v.y;
+            }
+            if (PREC == 0) {
+              uint4 hr, hm, lr, lm;
+              uint32_t* phr = &hr.x;
+              uint32_t* phm = &hm.x;
+              uint32_t* plr = &lr.x;
+              uint32_t* plm = &lm.x;
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const uint32_t a = __float_as_uint(re[m]) & 0xFFFFE000u, b = __float_as_uint(im[m]) & 0xFFFFE000u;
+                phr[m] = a;
+                phm[m] = b;
+                plr[m] = __float_as_uint(re[m] - __uint_as_float(a));
+                plm[m] = __float_as_uint(im[m] - __uint_as_float(b));
+              }
+              *reinterpret_cast<uint4*>(hi + ore[j]) = hr;
+              *reinterpret_cast<uint4*>(hi + oim[j]) = hm;
+              *reinterpret_cast<uint4*>(lo + ore[j]) = lr;
+              *reinterpret_cast<uint4*>(lo + oim[j]) = lm;
+            } else {
+              __align__(16) __nv_bfloat16 hr[8], hm[8], lr[8], lm[8];
+#pragma unroll
+              for (int m = 0; m < 8; ++m) {
+                hr[m] = __float2bfloat16_rn(re[m]);
+                hm[m] = __float2bfloat16_rn(im[m]);
+                lr[m] = __float2bfloat16_rn(re[m] - __bfloat162float(hr[m]));
+                lm[m] = __float2bfloat16_rn(im[m] - __bfloat162float(hm[m]));
+              }
+              *reinterpret_cast<uint4*>(hi + ore[j]) = *reinterpret_cast<const uint4*>(hr);
+              *reinterpret_cast<uint4*>(hi + oim[j]) = *reinterpret_cast<const uint4*>(hm);
+              *reinterpret_cast<uint4*>(lo + ore[j]) = *reinterpret_cast<const uint4*>(lr);
+              *reinterpret_cast<uint4*>(lo + oim[j]) = *reinterpret_cast<const uint4*>(lm);
+            }
+          }
+          fence_async_smem();
+          mbar_arrive(&full_b[s]);
         }
       }
-      fence_async_smem();
-      mbar_arrive(&full_b[s]);
-      if (it + 1 < nit) gather(g + (it + 1) * nG, v);
+      const bool ok = named_bar_and(1, NPROD, mine);  // also: every producer is done reading buffer wb
+      if (!ok) break;
+      consumed = w + 1;
+      if (tid == 0 && ky0 + issued < ky1) {
+        load_window(ky0 + issued, issued & 1);
+        ++issued;
+      }
     }
-  } else if (tid == 256) {
+    // windows still in flight after an abort land before the CTA's shared memory is released
+    if (tid == 0)
+      for (int w = consumed; w < issued; ++w) mbar_wait(&win_b[w & 1], (uint32_t)((w >> 1) & 1), GTC_MAXITER);
+  } else if (tid == 32 * (GTC_PROD_WARPS + 4)) {
     // ---------------- MMA issue (one thread, in a warp of its own) ----------------
     const uint32_t idesc = umma_idesc(PREC == 0 ? 2u : 1u, 128, Cp);
     for (int it = 0; it < nit; ++it) {
-      const int s = it % GTC_STAGES;
-      if (!gtc_wait(&full_b[s], (uint32_t)((it / GTC_STAGES) & 1), &s_abort)) break;
+      const int s = it % NST;
+      if (!gtc_wait(&full_b[s], (uint32_t)((it / NST) & 1), &s_abort)) break;
       const int ep = it / GTC_EPOCH;
       if (it % GTC_EPOCH == 0 && ep > 0 && !gtc_wait(&accempty_b, (uint32_t)((ep - 1) & 1), &s_abort)) break;
       tc_fence_after();
       const uint32_t hb = smem_u32(gsm + (size_t)s * 2 * arr_bytes), lb = hb + (uint32_t)arr_bytes;
       const uint32_t arow = (uint32_t)(128 * t / 8) * SBO;
-      const uint64_t ah = umma_desc(hb + arow, LBO, SBO), al = umma_desc(lb + arow, LBO, SBO);
-      const uint32_t acc0 = (it % GTC_EPOCH) ? 1u : 0u;  // a new epoch overwrites the accumulator
-      for (int h = need_h0 ? 0 : 1; h < 2; ++h) {
-        const uint32_t brow = (uint32_t)(h * Cp / 8) * SBO;
-        const uint64_t bh = umma_desc(hb + brow, LBO, SBO), bl = umma_desc(lb + brow, LBO, SBO);
-        const uint32_t d = tmem + (uint32_t)(h * Cp);
-        if (PREC == 0) {
-          umma_tf32(d, ah, bh, idesc, acc0);
-          umma_tf32(d, ah, bl, idesc, 1u);
-          umma_tf32(d, al, bh, idesc, 1u);
-        } else {
-          umma_bf16(d, ah, bh, idesc, acc0);
-          umma_bf16(d, ah, bl, idesc, 1u);
-          umma_bf16(d, al, bh, idesc, 1u);
+#pragma unroll
+      for (int ks = 0; ks < GTC_KSTEP; ++ks) {
+        const uint32_t kb = (uint32_t)ks * 2 * LBO;
+        const uint64_t ah = umma_desc(hb + arow + kb, LBO, SBO), al = umma_desc(lb + arow + kb, LBO, SBO);
+        // a new epoch overwrites the accumulator
+        const uint32_t acc0 = (it % GTC_EPOCH || ks) ? 1u : 0u;
+        for (int h = need_h0 ? 0 : 1; h < 2; ++h) {
+          const uint32_t brow = (uint32_t)(h * Cp / 8) * SBO + kb;
+          const uint64_t bh = umma_desc(hb + brow, LBO, SBO), bl = umma_desc(lb + brow, LBO, SBO);
+          const uint32_t d = tmem + (uint32_t)(h * Cp);
+          if (PREC == 0) {
+            umma_tf32(d, ah, bh, idesc, acc0);
+            umma_tf32(d, ah, bl, idesc, 1u);
+            umma_tf32(d, al, bh, idesc, 1u);
+          } else {
+            umma_bf16(d, ah, bh, idesc, acc0);
+            umma_bf16(d, ah, bl, idesc, 1u);
+            umma_bf16(d, al, bh, idesc, 1u);
+          }
         }
       }
       umma_commit(&empty_b[s]);
       if (it % GTC_EPOCH == GTC_EPOCH - 1 || it == nit - 1) umma_commit(&accfull_b);
     }
-  }
-  if (warp >= 4 && warp < 8) {
-    // ---------------- drain: each epoch's accumulator into the running sum ----------------
-    const int lw = warp & 3;
-    float* srow = Ssum + (size_t)(32 * lw + lane) * sld;
+    // every MMA issued above has finished before TMEM and the ring are released
+    umma_commit(&fin_b);
+    mbar_wait(&fin_b, 0u, GTC_MAXITER);
+  } else if (warp >= GTC_PROD_WARPS && warp < GTC_PROD_WARPS + 4) {
+    // ---------------- drain: each epoch's accumulator into this CTA's FP32 partial (L2) ----------------
+    const int lw = warp & 3;  // TMEM lanes 32 (warp % 4) .. +31 are this warp's
+    const int row = 128 * t + 32 * lw + lane;
+    float* orow = Rpart + ((size_t)lf * nG + g) * R2C * R2C + (size_t)row * R2C;
     for (int ep = 0; ep < nepoch; ++ep) {
-      if (!gtc_wait(&accfull_b, (uint32_t)(ep & 1), &s_abort)) break;
+      // warp-uniform: the TMEM loads below are .sync.aligned
+      if (!__all_sync(0xffffffffu, gtc_wait(&accfull_b, (uint32_t)(ep & 1), &s_abort))) break;
       tc_fence_after();
-      for (int c0 = c_begin; c0 < R2C; c0 += 8) {
-        uint32_t dv[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * lw) << 16) + (uint32_t)c0, dv);
+      // the first epoch stores, later ones add without reading back (no round trip to L2)
+      for (int c0 = c_begin; c0 < R2C; c0 += 16) {
+        uint32_t dv[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * lw) << 16) + (uint32_t)c0, dv);
+        if (row < R2C) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) srow[c0 + j] += __uint_as_float(dv[j]);
+          for (int q = 0; q < 4; ++q) {
+            const float v0 = __uint_as_float(dv[4 * q]), v1 = __uint_as_float(dv[4 * q + 1]);
+            const float v2 = __uint_as_float(dv[4 * q + 2]), v3 = __uint_as_float(dv[4 * q + 3]);
+            if (ep == 0)
+              *reinterpret_cast<float4*>(orow + c0 + 4 * q) = make_float4(v0, v1, v2, v3);
+            else
+              red_add_v4(orow + c0 + 4 * q, v0, v1, v2, v3);
+          }
+        }
       }
       tc_fence_before();
       mbar_arrive(&accempty_b);
     }
+    if (nepoch == 0 && row < R2C)
+      for (int c = c_begin; c < R2C; ++c) orow[c] = 0.f;
   }
   __syncthreads();
-  const bool ok = !s_abort;
-  if (!ok && tid == 0) atomicExch(errflag, SMSM_ERR_TIMEOUT);
-  float* out = Rpart + ((size_t)lf * nG + g) * R2C * R2C;
-  for (int e = tid; e < 128 * R2C; e += GTC_THREADS) {
-    const int rl = e / R2C, c = e - rl * R2C;
-    const int row = 128 * t + rl;
-    if (row < R2C && c >= c_begin) out[(size_t)row * R2C + c] = ok ? Ssum[(size_t)rl * sld + c] : 0.f;
-  }
+  if (s_abort && tid == 0) atomicExch(errflag, SMSM_ERR_TIMEOUT);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, R2C > 256 ? 512 : 256);
+  if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
 // G[c][c'] (c <= c') = sum_g (R[c][c'] + R[Cp+c][Cp+c']) + i (R[c][Cp+c'] - R[c'][Cp+c]) in FP64;
@@ -268,20 +355,24 @@ __global__ void k_gram_tc_reduce(const float* __restrict__ Rpart, double2* __res
   }
 }
 
-// 2Cp <= 288 TMEM columns and 3 staged chunks + the running sum in shared memory
-int gram_tc_supported(const smsm_plan_s* P) { return P->C <= 144; }
+static size_t gram_tc_smem_for(int C, int Ns, int r, int N) {
+  return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16)).total;
+}
+
+// 2Cp <= 288 TMEM columns; the ring and two patch-row windows in shared memory
+int gram_tc_supported(const smsm_plan_s* P) {
+  return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N) <= 224 * 1024;
+}
 
 int gram_tc_cp(const smsm_plan_s* P) { return 16 * ((P->C + 15) / 16); }
 
+// blocks of patch rows per (row tile, matrix): about four waves over 152 SMs when the
+// batch is large, more blocks (down to 2 patch rows each) when it is small
 int gram_tc_nG(const smsm_plan_s* P) {
-  const int P1 = P->P1;
   const int Cp = gram_tc_cp(P), R2C = 2 * Cp;
   const int ntile = (R2C + 127) / 128;
-  // enough CTAs for two waves over 152 SMs, at most ~8k patches per partial, at least 256
-  int nG = (P1 * P1 + 8191) / 8192;
-  const int waves = (2 * 152 + ntile * P->LD - 1) / (ntile * P->LD);
-  if (nG < waves) nG = waves;
-  const int most = (P1 * P1 + 255) / 256;
+  int nG = (4 * 152 + ntile * P->LD - 1) / (ntile * P->LD);
+  const int most = (P->P1 + 1) / 2;
   if (nG > most) nG = most;
   const size_t per = (size_t)P->LD * R2C * R2C * sizeof(float);
   int cap = (int)((size_t)256 * 1024 * 1024 / per);
@@ -291,16 +382,12 @@ int gram_tc_nG(const smsm_plan_s* P) {
   return nG;
 }
 
-static size_t gram_tc_smem(const smsm_plan_s* P) {
-  const int R2C = 2 * gram_tc_cp(P);
-  const int rows_alloc = 128 * ((R2C + 127) / 128);
-  return 2 * GTC_STAGES * (size_t)rows_alloc * 32 + (size_t)128 * (R2C + 1) * sizeof(float);
-}
+static size_t gram_tc_smem(const smsm_plan_s* P) { return gram_tc_smem_for(P->C, P->Ns, P->r, P->N); }
 
 smsm_status gram_tc_init_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024);
+    e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
   if (e != cudaSuccess) {
     smsm_set_error("cudaFuncSetAttribute (tensor-core Gram): %s", cudaGetErrorString(e));
     return SMSM_ERR_CUDA;
