@@ -79,9 +79,14 @@ typedef struct {
  */
 typedef enum { SMSM_PRECISION_FP32 = 0, SMSM_PRECISION_BF16_SPLIT = 1 } smsm_precision;
 
-/* smsm_opts.flags: use the shape-generic kernels even where a specialised fast
- * path exists (same results up to rounding; for testing and comparison). */
+/* smsm_opts.flags (same results up to rounding; for testing and comparison):
+ *   GENERIC_KERNELS: the shape-generic kernels even where a specialised fast
+ *                    path exists;
+ *   PER_COIL_NORMAL: the column stage of A^H A loops over the coils with two
+ *                    M-point transforms per coil instead of applying the
+ *                    per-class coil correlations (which need N % caipi_div == 0). */
 #define SMSM_FLAG_GENERIC_KERNELS 1
+#define SMSM_FLAG_PER_COIL_NORMAL 2
 
 /*
  * Solver parameters.  The paper minimises Eq. 10 with an augmented-Lagrangian
@@ -170,7 +175,9 @@ size_t smsm_plan_workspace_bytes(smsm_plan_t plan);
 /*
  * Set the coil sensitivities S (Fig. 1 step (ii)): sens is [L][Nc][N][N]
  * complex64, image domain.  The plan keeps its own copy (transposed for the
- * column kernels), so `sens` may be freed once the stream has passed this call.
+ * column kernels) and, where the CAIPI shift is a whole number of pixels, the
+ * coil correlations of every aliasing class of A^H A derived from it, so
+ * `sens` may be freed once the stream has passed this call.
  */
 smsm_status smsm_plan_set_sens(smsm_plan_t plan, const void* sens, void* stream);
 

@@ -96,7 +96,7 @@ static void free_plan(smsm_plan_s* P) {
                   P->yh,   P->phaseT, P->xs,    P->bv,   P->rv,    P->pv,    P->qv,   P->ybuf,
                   P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2,
                   P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep,
-                  P->Rpart, P->devflag};
+                  P->Rpart, P->devflag, P->acorr, P->ash};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (P->has_graph) cudaGraphExecDestroy(P->gexec);
@@ -178,6 +178,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     return SMSM_ERR_ARG;
   }
   if (P->precision == SMSM_PRECISION_BF16_SPLIT) P->gram_tc = 1;
+  P->alias = !(P->flags & (SMSM_FLAG_GENERIC_KERNELS | SMSM_FLAG_PER_COIL_NORMAL)) && alias_supported(P);
   P->P1 = N - r + 1;
   P->R2 = 2 * r - 1;
   P->fN = fN;
@@ -233,6 +234,10 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     const size_t R2C = 2 * (size_t)gram_tc_cp(P);
     A(Rpart, LD * P->gram_tc_nG * R2C * R2C);
   }
+  if (P->alias) {
+    A(acorr, alias_corr_count(P));
+    A(ash, (size_t)shots * shots);
+  }
   A(devflag, 1);
   A(rep, 1);
 #undef A
@@ -286,8 +291,16 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
       for (int n = 0; n < N; ++n) h[(size_t)d * N + n] = expi_frac((long long)(d - (r - 1)) * (n - N / 2), N);
     st = upload(P->Etab, h);
   }
+  if (!st && P->alias) {
+    // ash[i][q] = exp(-j 2 pi (i - N/2) q / Ns)
+    std::vector<float2> h((size_t)shots * shots);
+    for (int i = 0; i < shots; ++i)
+      for (int q = 0; q < shots; ++q) h[(size_t)i * shots + q] = expi_frac((long long)(i - N / 2) * q, shots);
+    st = upload(P->ash, h);
+  }
   if (!st) st = operators_init_attrs();
   if (!st) st = colfast_init_attrs();
+  if (!st) st = alias_init_attrs();
   if (!st) st = band_init_attrs(P);
   if (!st) st = gram_tc_init_attrs();
   if (!st) {
@@ -367,6 +380,7 @@ extern "C" smsm_status smsm_plan_set_sens(smsm_plan_t plan, const void* sens, vo
   CHECK_PLAN("smsm_plan_set_sens");
   CHECK_PTR("smsm_plan_set_sens", sens);
   smsm_status st = launch_transpose((const float2*)sens, plan->sensT, plan->L * plan->Nc, plan->N, plan->N, S(stream));
+  if (!st && plan->alias) st = launch_alias_corr(plan, S(stream));
   if (!st) plan->has_sens = 1;
   return st;
 }

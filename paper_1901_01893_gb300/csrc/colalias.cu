@@ -1,0 +1,232 @@
+// Column stage of (A^H A + lambda P_W) through the aliasing structure of A^H A.
+//
+// Every shot samples the k-space lines n = m Ns + i (m < M = N/Ns) of all
+// coils, and the readout direction is fully sampled, so in the image domain
+//   A^H A = S^H F_y^H Pi^H Pi F_y S        (Eqs. 1-3; Pi = CAIPI phase, slice
+//                                          sum and shot mask)
+// needs no transform at all.  Writing sh = N/Ldiv (the CAIPI shift of one
+// slice index) and u = y + l sh, the y transform restricted to the lines of
+// shot i followed by its adjoint sums exp(2 pi j m (u - u')/M) over m: it is
+// M when u = u' (mod M) and 0 otherwise.  What remains couples, for each image
+// column x and each class z = u mod M, the L Ns pixels (l, y) of that class:
+//
+//   (A^H A v)_{l,i}(y) = (1/Ns) conj(a_i^k) sum_{(l',y')} C_xz[(l,y),(l',y')] a_i^k' v_{l',i}(y'),
+//
+// with k = floor(u/M), a_i = exp(-2 pi j (i - N/2)/Ns) and the coil
+// correlation C_xz[(l,y),(l',y')] = sum_c conj(S_{c,l}(x,y)) S_{c,l'}(x,y').
+// C depends on the coil maps only, so it is formed once when they are set
+// (k_alias_corr) and shared by every shot, direction and iteration.  Per
+// pixel the coil loop (Nc coils x two M-point transforms) becomes L Ns complex
+// multiply-adds.  The class structure needs sh to be an integer: Ldiv | N.
+//
+// Member a = l Ns + t of class z is the pixel y = ((z - l sh) mod M) + t M of slice l.
+#include "common.cuh"
+#include "fft.cuh"
+
+// sC[x][z][a][a'] = sum_c conj(S_{c,l}(x, y_a)) S_{c,l'}(x, y_a'), FP64 accumulation
+__global__ void k_alias_corr(const float2* __restrict__ sensT, float2* __restrict__ corr, int L, int Ns, int Nc,
+                             int N, int M, int sh) {
+  const int B = L * Ns;
+  const size_t NN = (size_t)N * N;
+  const size_t total = (size_t)N * M * B * B;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int ap = (int)(e % B);
+    const int a = (int)((e / B) % B);
+    const int z = (int)((e / ((size_t)B * B)) % M);
+    const int x = (int)(e / ((size_t)B * B * M));
+    const int l = a / Ns, t = a - l * Ns, lp = ap / Ns, tp = ap - lp * Ns;
+    const int y = (z - (l * sh) % M + M) % M + t * M;
+    const int yp = (z - (lp * sh) % M + M) % M + tp * M;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < Nc; ++c) {
+      const float2 s = sensT[(size_t)(l * Nc + c) * NN + (size_t)x * N + y];
+      const float2 q = sensT[(size_t)(lp * Nc + c) * NN + (size_t)x * N + yp];
+      re += (double)s.x * q.x + (double)s.y * q.y;
+      im += (double)s.x * q.y - (double)s.y * q.x;
+    }
+    corr[e] = make_float2((float)re, (float)im);
+  }
+}
+
+// One CTA per (image column x, direction): hybrid lines -> image (F_y^-1), the
+// class products above plus lambda times the periodic penalty multiplier, the
+// partial of Re<img, acc>, and F_y back to hybrid lines.  Thread tid < N tpy
+// owns pixel row y = tid mod N of the lines b = tid / N (mod tpy); blockDim is
+// N tpy rounded up to whole warps (the extra threads only help with the FFTs).
+template <int L, int NS>
+__global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __restrict__ corr,
+                                                   const float2* __restrict__ ash, int sh, int tpy) {
+  constexpr int B = L * NS;
+  constexpr int CST = B * B + 1;  // padded class stride: consecutive classes start 2 banks apart
+  extern __shared__ float2 sm[];
+  const int N = a.N, M = a.M;
+  float2* img = sm;           // [B][N]
+  float2* tmp = img + B * N;  // [B][N]
+  float2* ph = tmp + B * N;   // [B][N] image times a_i^k
+  float2* sC = ph + B * N;    // [M][CST]
+  float2* sTwN = sC + M * CST;
+  float2* sAsh = sTwN + N;    // [NS][NS]: a_i^q, q < NS
+  double* red = reinterpret_cast<double*>(sAsh + NS * NS);  // [blockDim/32]
+  const int x = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t NN = (size_t)N * N;
+  const size_t dir = blockIdx.y;
+  const float2* __restrict__ gin = a.in + dir * (size_t)B * NN;
+  float2* __restrict__ gout = a.out + dir * (size_t)B * NN;
+  const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)B * NS * NN : nullptr;
+  double* gdot = a.dot_part ? a.dot_part + dir * SMSM_PART_MAX : nullptr;
+
+  for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
+  for (int e = tid; e < NS * NS; e += nt) sAsh[e] = ash[e];
+  {
+    const float2* cx = corr + (size_t)x * M * B * B;
+    for (int e = tid; e < M * B * B; e += nt) {
+      const int z = e / (B * B);
+      sC[z * CST + (e - z * B * B)] = cx[e];
+    }
+  }
+  const bool own = tid < N * tpy;
+  const int y = tid % N, bsub = own ? tid / N : B;
+  // hybrid lines -> image lines (F_y^-1)
+  const float sy = sgn_par(y);
+  for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(gin[(size_t)b * NN + (size_t)x * N + y], sy);
+  __syncthreads();
+  {
+    float2* R = fft_smem<true>(img, tmp, B, N, a.fN, sTwN);
+    const float sc = a.sN * sy;
+    for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(R[b * N + y], sc);
+  }
+  // this pixel's class z, block k (mod NS) and member row in every slice
+  const int t = y / M;
+  int zl[L], kl[L], bs[L][L];  // (idle threads: bsub = B keeps every loop below empty)
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const int u = y + l * sh;
+    zl[l] = u % M;
+    kl[l] = (u / M) % NS;
+  }
+#pragma unroll
+  for (int l = 0; l < L; ++l)
+#pragma unroll
+    for (int lp = 0; lp < L; ++lp) {
+      int d = zl[l] - (lp * sh) % M;
+      bs[l][lp] = d < 0 ? d + M : d;
+    }
+  __syncthreads();
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    int i0 = (bsub - l * NS) % tpy;
+    if (i0 < 0) i0 += tpy;
+    if (!own) i0 = NS;
+    for (int i = i0; i < NS; i += tpy) ph[(l * NS + i) * N + y] = cmul(sAsh[i * NS + kl[l]], img[(l * NS + i) * N + y]);
+  }
+  __syncthreads();
+
+  const bool pen = gmult != nullptr && a.lambda != 0.f;
+  const float inv_ns = 1.f / (float)NS;
+  float dsum = 0.f;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    float2 c[B];  // row (l, t) of this pixel's class matrix, shared by every shot
+    const float2* crow = sC + zl[l] * CST + (l * NS + t) * B;
+#pragma unroll
+    for (int ap = 0; ap < B; ++ap) c[ap] = crow[ap];
+    int i0 = (bsub - l * NS) % tpy;
+    if (i0 < 0) i0 += tpy;
+    if (!own) i0 = NS;
+    for (int i = i0; i < NS; i += tpy) {
+      const int b = l * NS + i;
+      float2 s = cmk(0.f, 0.f);
+#pragma unroll
+      for (int lp = 0; lp < L; ++lp) {
+        const float2* prow = ph + (lp * NS + i) * N + bs[l][lp];
+#pragma unroll
+        for (int tp = 0; tp < NS; ++tp) cfma(s, c[lp * NS + tp], prow[tp * M]);
+      }
+      float2 acc = cscale(cmulcj(sAsh[i * NS + kl[l]], s), inv_ns);
+      const float2 v = img[b * N + y];
+      if (pen) {
+        float2 q = cmk(0.f, 0.f);
+        const float2* mrow = gmult + (size_t)b * NS * NN + (size_t)x * N + y;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) cfma(q, mrow[(size_t)j * NN], img[(l * NS + j) * N + y]);
+        acc.x = fmaf(a.lambda, q.x, acc.x);
+        acc.y = fmaf(a.lambda, q.y, acc.y);
+      }
+      dsum = fmaf(v.x, acc.x, fmaf(v.y, acc.y, dsum));
+      tmp[b * N + y] = cscale(acc, sy);
+    }
+  }
+  // partial of Re<img, acc> (Parseval: equals Re<p, q> in k-space); FP32 over this
+  // thread's few pixels, FP64 from there on
+  double dd = (double)dsum;
+  for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+  if ((tid & 31) == 0) red[tid >> 5] = dd;
+  __syncthreads();
+  if (tid == 0 && gdot) {
+    double s2 = 0.0;
+    for (int w = 0; w < nt / 32; ++w) s2 += red[w];
+    gdot[x] = s2;
+  }
+  float2* Rr = fft_smem<false>(tmp, ph, B, N, a.fN, sTwN);
+  const float so = a.sN * sy;
+  for (int b = bsub; b < B; b += tpy) gout[(size_t)b * NN + (size_t)x * N + y] = cscale(Rr[b * N + y], so);
+}
+
+typedef void (*ColAliasFn)(ColArgs, const float2*, const float2*, int, int);
+
+#define CA_NS(L) {k_col_alias<L, 1>, k_col_alias<L, 2>, k_col_alias<L, 3>, k_col_alias<L, 4>, \
+                  k_col_alias<L, 5>, k_col_alias<L, 6>, k_col_alias<L, 7>, k_col_alias<L, 8>}
+static const ColAliasFn kColAlias[3][8] = {CA_NS(1), CA_NS(2), CA_NS(3)};
+#undef CA_NS
+
+// threads per pixel row: at least 64 threads per CTA
+static int alias_tpy(int N) { return N >= 64 ? 1 : (64 + N - 1) / N; }
+
+static int alias_threads(int N) { return (N * alias_tpy(N) + 31) / 32 * 32; }
+
+static size_t alias_smem(const smsm_plan_s* P) {
+  const int B = P->L * P->Ns;
+  const int nt = alias_threads(P->N);
+  return (size_t)(3 * B * P->N + P->M * (B * B + 1) + P->N + P->Ns * P->Ns) * sizeof(float2) +
+         (size_t)((nt + 31) / 32) * sizeof(double);
+}
+
+size_t alias_corr_count(const smsm_plan_s* P) {
+  const size_t B = (size_t)P->L * P->Ns;
+  return (size_t)P->N * P->M * B * B;
+}
+
+int alias_supported(const smsm_plan_s* P) {
+  if (P->N % P->Ldiv) return 0;  // CAIPI shift must be a whole number of pixels
+  if (P->L < 1 || P->L > 3 || P->Ns < 1 || P->Ns > 8) return 0;
+  if (alias_threads(P->N) > 512) return 0;
+  if (alias_corr_count(P) * sizeof(float2) > (size_t)256 * 1024 * 1024) return 0;
+  return alias_smem(P) <= 200 * 1024;
+}
+
+smsm_status alias_init_attrs() {
+  for (int l = 0; l < 3; ++l)
+    for (int n = 0; n < 8; ++n) {
+      cudaError_t e = cudaFuncSetAttribute(kColAlias[l][n], cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) {
+        smsm_set_error("cudaFuncSetAttribute (aliasing column stage): %s", cudaGetErrorString(e));
+        return SMSM_ERR_CUDA;
+      }
+    }
+  return SMSM_OK;
+}
+
+smsm_status launch_alias_corr(const smsm_plan_s* P, cudaStream_t s) {
+  k_alias_corr<<<1024, 256, 0, s>>>(P->sensT, P->acorr, P->L, P->Ns, P->Nc, P->N, P->M, P->N / P->Ldiv);
+  SMSM_LAUNCH_CHECK("k_alias_corr");
+  return SMSM_OK;
+}
+
+smsm_status launch_col_alias(const smsm_plan_s* P, const ColArgs& a, cudaStream_t s) {
+  const int tpy = alias_tpy(P->N);
+  kColAlias[P->L - 1][P->Ns - 1]<<<dim3(P->N, P->D), alias_threads(P->N), alias_smem(P), s>>>(a, P->acorr, P->ash,
+                                                                                      P->N / P->Ldiv, tpy);
+  SMSM_LAUNCH_CHECK("k_col_alias");
+  return SMSM_OK;
+}

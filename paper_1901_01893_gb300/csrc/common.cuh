@@ -80,6 +80,9 @@ struct smsm_plan_s {
   int gram_tc;    // 1: tensor-core Gram
   int gram_tc_nG; // split-K partials of the tensor-core Gram
   float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials
+  int alias;      // 1: column stage of A^H A through the per-class coil correlations
+  float2* acorr;  // [N(x)][M(class)][L Ns][L Ns] coil correlations of the aliasing classes
+  float2* ash;    // [Ns][Ns]: exp(-2 pi j (i - N/2) q / Ns)
   int* devflag;   // device error flag raised by bounded waits (SMSM_ERR_TIMEOUT)
   int LD;  // D * L: number of (direction, slice) Hankel matrices
   int nband;  // pixels within r-1 of an edge
@@ -220,6 +223,12 @@ smsm_status colfast_init_attrs();
 smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const float2* in, float2* out,
                        const float2* phaseT, const float2* multT, float lambda, double* dot_part,
                        cudaStream_t s);
+// colalias.cu: column stage of (A^H A + lambda P_W) through the aliasing classes
+int alias_supported(const smsm_plan_s* P);
+size_t alias_corr_count(const smsm_plan_s* P);
+smsm_status alias_init_attrs();
+smsm_status launch_alias_corr(const smsm_plan_s* P, cudaStream_t s);
+smsm_status launch_col_alias(const smsm_plan_s* P, const ColArgs& a, cudaStream_t s);
 // hankel.cu
 smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
 // gram_tc.cu

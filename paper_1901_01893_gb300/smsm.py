@@ -19,6 +19,7 @@ SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
 SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_FLAG_GENERIC_KERNELS = 1
+SMSM_FLAG_PER_COIL_NORMAL = 2
 SMSM_PRECISION_FP32, SMSM_PRECISION_BF16_SPLIT = 0, 1
 SMSM_MAX_OUTER = 128
 STAGES = ["adjoint", "gram", "eig", "vapply", "weights", "filters", "rowfft_inv", "column", "rowfft_fwd",

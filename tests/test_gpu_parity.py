@@ -281,32 +281,36 @@ def test_batch_matches_single_problems(smsm):
     assert O.nrmse(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
 
 
-@pytest.mark.parametrize("L,Ns,Nc,N,r", [
-    (2, 4, 8, 64, 5),    # M = 16 (lane segments)
-    (3, 8, 6, 64, 3),    # M = 8, three slices
-    (2, 4, 8, 128, 6),   # M = 32
-    (2, 2, 6, 128, 4),   # M = 64 (local radix-2)
-    (1, 2, 4, 192, 4),   # M = 96 (local radix-3), one slice
-    (3, 2, 4, 256, 4),   # M = 128 (local radix-4)
-    (1, 3, 5, 96, 3),    # N = 96, M = 32
+@pytest.mark.parametrize("L,Ns,Nc,N,r,Ldiv", [
+    (2, 4, 8, 64, 5, 0),    # M = 16 (lane segments)
+    (3, 4, 6, 64, 3, 8),    # CAIPI shift N/8: classes pair pixels 8 apart within M = 16
+    (3, 2, 5, 64, 3, 4),    # CAIPI shift N/4 = M/2
+    (3, 8, 6, 64, 3, 0),    # M = 8, three slices
+    (2, 4, 8, 128, 6, 0),   # M = 32
+    (2, 2, 6, 128, 4, 0),   # M = 64 (local radix-2)
+    (1, 2, 4, 192, 4, 0),   # M = 96 (local radix-3), one slice
+    (3, 2, 4, 256, 4, 0),   # M = 128 (local radix-4); 256 % 3 != 0: no aliasing classes
+    (1, 3, 5, 96, 3, 0),    # N = 96, M = 32
 ])
-def test_fast_column_stage_matches_generic(smsm, L, Ns, Nc, N, r):
-    # the warp-shuffle column stage and the shape-generic one compute the same
-    # (A^H A + lambda P_W); compare whole (short) solves, and one against the oracle
+def test_fast_column_stage_matches_generic(smsm, L, Ns, Nc, N, r, Ldiv):
+    # the aliasing-class column stage, the warp-shuffle per-coil one and the
+    # shape-generic one compute the same (A^H A + lambda P_W); compare whole
+    # (short) solves, and one against the oracle
     rng = np.random.default_rng(L * 100 + N + Ns)
     S = crandn(rng, L, Nc, N, N) / np.sqrt(Nc)
     y = crandn(rng, Ns, Nc, N // Ns, N)
     prm = smsm.default_params(lam=3e-2, outer_iters=2, cg_iters=3)
     out = []
-    for flags in (0, smsm.SMSM_FLAG_GENERIC_KERNELS):
-        p = smsm.Plan(L, Ns, Nc, N, r, flags=flags)
+    for flags in (0, smsm.SMSM_FLAG_PER_COIL_NORMAL, smsm.SMSM_FLAG_GENERIC_KERNELS):
+        p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, flags=flags)
         p.set_sens(c64(S))
         x, rep = p.reconstruct(c64(y), params=prm)
         assert rep.status == 0
         out.append(x.cpu().numpy())
-    assert O.nrmse(out[0], out[1]) < 1e-5
+    assert O.nrmse(out[0], out[2]) < 1e-5
+    assert O.nrmse(out[1], out[2]) < 1e-5
     if N <= 128:
-        ref = O.reconstruct(y, S, r, dict(K=2, J=3, lam=3e-2))
+        ref = O.reconstruct(y, S, r, dict(K=2, J=3, lam=3e-2), Ldiv=Ldiv or L)
         assert O.nrmse(out[0], ref) < 1e-4
 
 
