@@ -22,6 +22,7 @@
 // Member a = l Ns + t of class z is the pixel y = ((z - l sh) mod M) + t M of slice l.
 #include "common.cuh"
 #include "fft.cuh"
+#include "umma.cuh"
 
 // sC[x][z][a][a'] = sum_c conj(S_{c,l}(x, y_a)) S_{c,l'}(x, y_a'), FP64 accumulation
 __global__ void k_alias_corr(const float2* __restrict__ sensT, float2* __restrict__ corr, int L, int Ns, int Nc,
@@ -48,25 +49,43 @@ __global__ void k_alias_corr(const float2* __restrict__ sensT, float2* __restric
   }
 }
 
+#define ALIAS_MAXITER (1L << 22)
+
+// bounded wait on an mbarrier phase; false when it ran out
+__device__ __forceinline__ bool alias_wait(uint64_t* mbar, uint32_t parity) {
+  for (long it = 0; it < ALIAS_MAXITER; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
 // One CTA per (image column x, direction): hybrid lines -> image (F_y^-1), the
 // class products above plus lambda times the periodic penalty multiplier, the
 // partial of Re<img, acc>, and F_y back to hybrid lines.  Thread tid < N tpy
 // owns pixel row y = tid mod N of the lines b = tid / N (mod tpy); blockDim is
 // N tpy rounded up to whole warps (the extra threads only help with the FFTs).
+// Thread 0 starts TMA bulk copies of the column's B hybrid lines and (when
+// msm, i.e. they fit in shared memory) its B Ns multiplier rows as soon as the
+// CTA starts, so the HBM reads overlap the set-up and the first transform.
 template <int L, int NS>
 __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __restrict__ corr,
-                                                   const float2* __restrict__ ash, int sh, int tpy) {
+                                                   const float2* __restrict__ ash, int sh, int tpy, int msm) {
   constexpr int B = L * NS;
-  constexpr int CST = B * B + 1;  // padded class stride: consecutive classes start 2 banks apart
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
+  __shared__ __align__(8) uint64_t bar[2];  // 0: hybrid lines, 1: multiplier rows
   const int N = a.N, M = a.M;
   float2* img = sm;           // [B][N]
   float2* tmp = img + B * N;  // [B][N]
   float2* ph = tmp + B * N;   // [B][N] image times a_i^k
-  float2* sC = ph + B * N;    // [M][CST]
-  float2* sTwN = sC + M * CST;
-  float2* sAsh = sTwN + N;    // [NS][NS]: a_i^q, q < NS
-  double* red = reinterpret_cast<double*>(sAsh + NS * NS);  // [blockDim/32]
+  float2* sTwN = ph + B * N;  // [N]
+  float2* sAsh = sTwN + N;    // [NS][NS]: a_i^q, q < NS (padded to 16 bytes)
+  double* red = reinterpret_cast<double*>(sAsh + ((NS * NS + 1) & ~1));  // [32]
+  float2* sM = reinterpret_cast<float2*>(red + 32);  // [B][NS][N] (msm)
   const int x = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t NN = (size_t)N * N;
@@ -75,27 +94,27 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
   float2* __restrict__ gout = a.out + dir * (size_t)B * NN;
   const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)B * NS * NN : nullptr;
   double* gdot = a.dot_part ? a.dot_part + dir * SMSM_PART_MAX : nullptr;
+  const bool pen = gmult != nullptr && a.lambda != 0.f;
+  const bool use_sm = pen && msm;
+  const uint32_t row_bytes = (uint32_t)(N * sizeof(float2));
 
-  for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
-  for (int e = tid; e < NS * NS; e += nt) sAsh[e] = ash[e];
-  {
-    const float2* cx = corr + (size_t)x * M * B * B;
-    for (int e = tid; e < M * B * B; e += nt) {
-      const int z = e / (B * B);
-      sC[z * CST + (e - z * B * B)] = cx[e];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    mbar_arrive_expect_tx(&bar[0], (uint32_t)B * row_bytes);
+    for (int b = 0; b < B; ++b) tma_bulk_g2s(img + b * N, gin + (size_t)b * NN + (size_t)x * N, row_bytes, &bar[0]);
+    if (use_sm) {
+      mbar_arrive_expect_tx(&bar[1], (uint32_t)(B * NS) * row_bytes);
+      for (int q = 0; q < B * NS; ++q)
+        tma_bulk_g2s(sM + q * N, gmult + (size_t)q * NN + (size_t)x * N, row_bytes, &bar[1]);
     }
   }
+  for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
+  for (int e = tid; e < NS * NS; e += nt) sAsh[e] = ash[e];
   const bool own = tid < N * tpy;
   const int y = tid % N, bsub = own ? tid / N : B;
-  // hybrid lines -> image lines (F_y^-1)
   const float sy = sgn_par(y);
-  for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(gin[(size_t)b * NN + (size_t)x * N + y], sy);
-  __syncthreads();
-  {
-    float2* R = fft_smem<true>(img, tmp, B, N, a.fN, sTwN);
-    const float sc = a.sN * sy;
-    for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(R[b * N + y], sc);
-  }
   // this pixel's class z, block k (mod NS) and member row in every slice
   const int t = y / M;
   int zl[L], kl[L], bs[L][L];  // (idle threads: bsub = B keeps every loop below empty)
@@ -112,6 +131,24 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
       int d = zl[l] - (lp * sh) % M;
       bs[l][lp] = d < 0 ? d + M : d;
     }
+  __syncthreads();  // barrier initialisation visible before anyone waits on it
+  // every thread agrees on the outcome of the waits, so none is left at a barrier
+  if (!__syncthreads_and(alias_wait(&bar[0], 0))) {
+    if (tid == 0) {
+      atomicExch(a.errflag, SMSM_ERR_TIMEOUT);
+      alias_wait(&bar[0], 0);  // in-flight copies land before the CTA exits
+      if (use_sm) alias_wait(&bar[1], 0);
+    }
+    return;
+  }
+  // hybrid lines -> image lines (F_y^-1)
+  for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(img[b * N + y], sy);
+  __syncthreads();
+  {
+    float2* R = fft_smem_call<true>(img, tmp, B, N, a.fN, sTwN);
+    const float sc = a.sN * sy;
+    for (int b = bsub; b < B; b += tpy) img[b * N + y] = cscale(R[b * N + y], sc);
+  }
   __syncthreads();
 #pragma unroll
   for (int l = 0; l < L; ++l) {
@@ -120,17 +157,26 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
     if (!own) i0 = NS;
     for (int i = i0; i < NS; i += tpy) ph[(l * NS + i) * N + y] = cmul(sAsh[i * NS + kl[l]], img[(l * NS + i) * N + y]);
   }
-  __syncthreads();
+  const bool mult_ok = !use_sm || alias_wait(&bar[1], 0);
+  if (!__syncthreads_and(mult_ok)) {
+    if (tid == 0) {
+      atomicExch(a.errflag, SMSM_ERR_TIMEOUT);
+      alias_wait(&bar[1], 0);  // in-flight copies land before the CTA exits
+    }
+    return;
+  }
 
-  const bool pen = gmult != nullptr && a.lambda != 0.f;
   const float inv_ns = 1.f / (float)NS;
+  const float2* cx = corr + (size_t)x * M * B * B;
   float dsum = 0.f;
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     float2 c[B];  // row (l, t) of this pixel's class matrix, shared by every shot
-    const float2* crow = sC + zl[l] * CST + (l * NS + t) * B;
+    const float2* crow = cx + ((size_t)zl[l] * B + (l * NS + t)) * B;
+    if (own) {
 #pragma unroll
-    for (int ap = 0; ap < B; ++ap) c[ap] = crow[ap];
+      for (int ap = 0; ap < B; ++ap) c[ap] = __ldg(crow + ap);
+    }
     int i0 = (bsub - l * NS) % tpy;
     if (i0 < 0) i0 += tpy;
     if (!own) i0 = NS;
@@ -147,9 +193,15 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
       const float2 v = img[b * N + y];
       if (pen) {
         float2 q = cmk(0.f, 0.f);
-        const float2* mrow = gmult + (size_t)b * NS * NN + (size_t)x * N + y;
+        if (use_sm) {
+          const float2* mrow = sM + b * NS * N + y;
 #pragma unroll
-        for (int j = 0; j < NS; ++j) cfma(q, mrow[(size_t)j * NN], img[(l * NS + j) * N + y]);
+          for (int j = 0; j < NS; ++j) cfma(q, mrow[j * N], img[(l * NS + j) * N + y]);
+        } else {
+          const float2* mrow = gmult + (size_t)b * NS * NN + (size_t)x * N + y;
+#pragma unroll
+          for (int j = 0; j < NS; ++j) cfma(q, mrow[(size_t)j * NN], img[(l * NS + j) * N + y]);
+        }
         acc.x = fmaf(a.lambda, q.x, acc.x);
         acc.y = fmaf(a.lambda, q.y, acc.y);
       }
@@ -168,28 +220,43 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
     for (int w = 0; w < nt / 32; ++w) s2 += red[w];
     gdot[x] = s2;
   }
-  float2* Rr = fft_smem<false>(tmp, ph, B, N, a.fN, sTwN);
+  float2* Rr = fft_smem_call<false>(tmp, ph, B, N, a.fN, sTwN);
   const float so = a.sN * sy;
   for (int b = bsub; b < B; b += tpy) gout[(size_t)b * NN + (size_t)x * N + y] = cscale(Rr[b * N + y], so);
 }
 
-typedef void (*ColAliasFn)(ColArgs, const float2*, const float2*, int, int);
+typedef void (*ColAliasFn)(ColArgs, const float2*, const float2*, int, int, int);
 
 #define CA_NS(L) {k_col_alias<L, 1>, k_col_alias<L, 2>, k_col_alias<L, 3>, k_col_alias<L, 4>, \
                   k_col_alias<L, 5>, k_col_alias<L, 6>, k_col_alias<L, 7>, k_col_alias<L, 8>}
 static const ColAliasFn kColAlias[3][8] = {CA_NS(1), CA_NS(2), CA_NS(3)};
 #undef CA_NS
 
-// threads per pixel row: at least 64 threads per CTA
-static int alias_tpy(int N) { return N >= 64 ? 1 : (64 + N - 1) / N; }
+// threads per pixel row: at least 64 threads per CTA (more threads per row measured slower:
+// each one then re-reads the class rows for fewer outputs)
+static int alias_tpy(int N, int B) {
+  const int t = N >= 64 ? 1 : (64 + N - 1) / N;
+  return t > B ? B : t;
+}
 
-static int alias_threads(int N) { return (N * alias_tpy(N) + 31) / 32 * 32; }
+static int alias_threads(int N, int B) { return (N * alias_tpy(N, B) + 31) / 32 * 32; }
+
+// the column's B Ns multiplier rows are staged in shared memory up to this size
+#define ALIAS_MSM_MAX (64 * 1024)
+
+static size_t alias_smem_base(const smsm_plan_s* P) {
+  const int B = P->L * P->Ns;
+  return (size_t)(3 * B * P->N + P->N + ((P->Ns * P->Ns + 1) & ~1)) * sizeof(float2) + 32 * sizeof(double);
+}
+
+static size_t alias_msm_bytes(const smsm_plan_s* P) {
+  return (size_t)P->L * P->Ns * P->Ns * P->N * sizeof(float2);
+}
+
+static int alias_msm(const smsm_plan_s* P) { return alias_msm_bytes(P) <= ALIAS_MSM_MAX; }
 
 static size_t alias_smem(const smsm_plan_s* P) {
-  const int B = P->L * P->Ns;
-  const int nt = alias_threads(P->N);
-  return (size_t)(3 * B * P->N + P->M * (B * B + 1) + P->N + P->Ns * P->Ns) * sizeof(float2) +
-         (size_t)((nt + 31) / 32) * sizeof(double);
+  return alias_smem_base(P) + (alias_msm(P) ? alias_msm_bytes(P) : 0);
 }
 
 size_t alias_corr_count(const smsm_plan_s* P) {
@@ -200,7 +267,7 @@ size_t alias_corr_count(const smsm_plan_s* P) {
 int alias_supported(const smsm_plan_s* P) {
   if (P->N % P->Ldiv) return 0;  // CAIPI shift must be a whole number of pixels
   if (P->L < 1 || P->L > 3 || P->Ns < 1 || P->Ns > 8) return 0;
-  if (alias_threads(P->N) > 512) return 0;
+  if (alias_threads(P->N, P->L * P->Ns) > 512) return 0;
   if (alias_corr_count(P) * sizeof(float2) > (size_t)256 * 1024 * 1024) return 0;
   return alias_smem(P) <= 200 * 1024;
 }
@@ -224,9 +291,9 @@ smsm_status launch_alias_corr(const smsm_plan_s* P, cudaStream_t s) {
 }
 
 smsm_status launch_col_alias(const smsm_plan_s* P, const ColArgs& a, cudaStream_t s) {
-  const int tpy = alias_tpy(P->N);
-  kColAlias[P->L - 1][P->Ns - 1]<<<dim3(P->N, P->D), alias_threads(P->N), alias_smem(P), s>>>(a, P->acorr, P->ash,
-                                                                                      P->N / P->Ldiv, tpy);
+  const int tpy = alias_tpy(P->N, P->L * P->Ns);
+  kColAlias[P->L - 1][P->Ns - 1]<<<dim3(P->N, P->D), alias_threads(P->N, P->L * P->Ns), alias_smem(P), s>>>(
+      a, P->acorr, P->ash, P->N / P->Ldiv, tpy, alias_msm(P));
   SMSM_LAUNCH_CHECK("k_col_alias");
   return SMSM_OK;
 }

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) k_col_fast(ColArgs a) {
   }
   __syncthreads();
   {
-    float2* R = fft_smem<true>(img, tmp, B, N, a.fN, sTwN);
+    float2* R = fft_fixed_from<true, N, 1>(img, tmp, B, N, sTwN);
     for (int e = tid; e < B * N; e += nt) img[e] = cscale(R[e], a.sN * sgn_par(e % N));
   }
   __syncthreads();
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_col_fast(ColArgs a) {
     for (int w = 0; w < Ns; ++w) s += red[w];
     gdot[x] = s;
   }
-  float2* Rr = fft_smem<false>(tmp, img, B, N, a.fN, sTwN);
+  float2* Rr = fft_fixed_from<false, N, 1>(tmp, img, B, N, sTwN);
   for (int e = tid; e < B * N; e += nt) {
     const int b = e / N, ky = e - b * N;
     gout[(size_t)b * NN + (size_t)x * N + ky] = cscale(Rr[e], a.sN * sgn_par(ky));

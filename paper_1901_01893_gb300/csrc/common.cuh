@@ -38,6 +38,16 @@ __device__ __forceinline__ void cfmacj(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
 
+// asynchronous 8-byte global -> shared copy (completes at cp_async_wait_all)
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 // ----------------------------------------------------------------------------
 // FFT descriptor: length n = prod(rad[0..np)), radices in {2, 3, 4}.
 // ----------------------------------------------------------------------------
@@ -213,6 +223,7 @@ struct ColArgs {
   int L, Ns, Nc, N, M;
   float sN, lambda;
   double* dot_part;  // [N] per-CTA partial of Re<img, acc> (nullable)
+  int* errflag;      // device error flag (bounded waits that ran out)
 };
 
 // colfast.cu: warp-shuffle column stage of (A^H A + lambda P_W); returns SMSM_ERR_ARG when the

@@ -48,13 +48,66 @@ __device__ __forceinline__ void dft3(float2* v) {
   v[2] = csub(m, j);
 }
 
+// One radix-R pass (R in {2, 3, 4}) of the Stockham FFT described above, with
+// the transform length N, R and the product S of the earlier radices fixed at
+// compile time (so every index division is by a constant); then the next pass.
+// Radices are taken in the order 4, ..., 4, 2, ..., 2, 3, ..., 3, the same
+// order as the runtime descriptor, so both give identical results.
+template <bool INV, int N, int S>
+__device__ __forceinline__ float2* fft_fixed_from(float2* src, float2* dst, int nbatch, int bstride,
+                                                  const float2* tw) {
+  if constexpr (S == N) {
+    return src;
+  } else {
+    constexpr int REM = N / S;
+    constexpr int R = (REM % 4 == 0) ? 4 : ((REM % 2 == 0) ? 2 : 3);
+    constexpr int nR = N / R;
+    constexpr int tstep = N / (S * R);
+    const int ntask = nbatch * nR;
+    for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+      const int bb = t / nR;
+      const int j = t - bb * nR;
+      const float2* Sp = src + bb * bstride;
+      float2* Dp = dst + bb * bstride;
+      const int k = j % S;
+      const int base = (j - k) * R + k;
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = Sp[j + r * nR];
+      if (S > 1 && k) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_get<INV>(tw, r * k * tstep));
+      }
+      if constexpr (R == 4)
+        dft4<INV>(v);
+      else if constexpr (R == 2)
+        dft2<INV>(v);
+      else
+        dft3<INV>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r) Dp[base + r * S] = v[r];
+    }
+    __syncthreads();
+    return fft_fixed_from<INV, N, S * R>(dst, src, nbatch, bstride, tw);
+  }
+}
+
 // Batched FFT of `nbatch` transforms of length d.n; transform b starts at
 // a + b*bstride (and b + b*bstride for the ping-pong buffer).  All threads
 // of the block take part; the routine ends with __syncthreads() after every
-// pass and returns the buffer that holds the result.  Unnormalised.
+// pass and returns the buffer that holds the result.  Unnormalised.  The
+// common lengths run a compile-time pass chain.
 template <bool INV>
 __device__ float2* fft_smem(float2* a, float2* b, int nbatch, int bstride, const FftDesc& d,
                             const float2* tw) {
+  switch (d.n) {
+    case 64: return fft_fixed_from<INV, 64, 1>(a, b, nbatch, bstride, tw);
+    case 96: return fft_fixed_from<INV, 96, 1>(a, b, nbatch, bstride, tw);
+    case 128: return fft_fixed_from<INV, 128, 1>(a, b, nbatch, bstride, tw);
+    case 192: return fft_fixed_from<INV, 192, 1>(a, b, nbatch, bstride, tw);
+    case 256: return fft_fixed_from<INV, 256, 1>(a, b, nbatch, bstride, tw);
+    default: break;
+  }
   const int n = d.n;
   int s = 1;
   float2* src = a;
@@ -109,6 +162,14 @@ __device__ float2* fft_smem(float2* a, float2* b, int nbatch, int bstride, const
     s *= R;
   }
   return src;
+}
+
+// fft_smem as an out-of-line call: kernels instantiated many times over other
+// template parameters share one copy of every pass chain
+template <bool INV>
+__device__ __noinline__ float2* fft_smem_call(float2* a, float2* b, int nbatch, int bstride, const FftDesc& d,
+                                              const float2* tw) {
+  return fft_smem<INV>(a, b, nbatch, bstride, d, tw);
 }
 
 // (-1)^n as a float

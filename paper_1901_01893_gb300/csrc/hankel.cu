@@ -249,16 +249,15 @@ smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s
 // ---------------------------------------------------------------------------
 // Border band: out[n] += scale * (P_valid(x)[n] - P_periodic(x)[n]) for the
 // pixels within r-1 of an edge, with the per-class taps dcls; optional
-// per-CTA partial of Re<x, scale*corr>.
-// The band is four strips: top (rows 0..r-2) and bottom (rows N-r+1..N-1) over
-// all columns, left/right (columns 0..r-2, N-r+1..N-1) over the interior rows.
-// A CTA takes BAND_TX pixels of one strip line, stages the (periodically
-// wrapped) x window of every shot and the line's class taps in shared memory,
-// and each thread accumulates all Ns output shots of its pixel.  Pixels at the
-// ends of a top/bottom line (the corners) have their own class and read their
-// taps from global memory.
+// partials of Re<x, scale*corr>.
+// The band is four strips -- top (rows 0..r-2) and bottom (rows N-r+1..N-1),
+// left and right (columns 0..r-2, N-r+1..N-1), each over the interior range
+// [r-1, N-r] of the other coordinate -- plus the four (r-1) x (r-1) corners.
+// Every pixel of a strip line has the same class, so k_band stages the line's
+// taps once per CTA; the corner pixels each have their own class and are
+// summed by k_band_corner.
 // ---------------------------------------------------------------------------
-#define BAND_P 2                  // pixels per thread
+#define BAND_P 4                  // pixels per thread
 #define BAND_TX (32 * BAND_P)     // pixels per strip line per CTA
 
 // One CTA = one chunk of BAND_TX pixels of one line of one strip; warp j sums
@@ -266,12 +265,14 @@ smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s
 // (pixel, output shot) are then added in a fixed order (deterministic).  The
 // line's window of x (2r-1 lines across, BAND_TX + 2r-2 along, periodically
 // wrapped) is staged in shared memory as [shot][across][along] for both
-// orientations; taps are warp-uniform loads (L1 broadcast).
+// orientations, and so are the line's taps [j][d][i] (read as broadcasts); both
+// with asynchronous copies, all in flight at once.  Lane q owns the pixels
+// q + 32 p (p < BAND_P), so the window reads of a warp are consecutive.
 template <int NS>
-__global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, float2* __restrict__ out,
-                                              const float2* __restrict__ dcls, int L, int N, int r, float scale,
-                                              double* __restrict__ dot_part) {
-  extern __shared__ float2 bsm[];
+__global__ void __launch_bounds__(32 * NS) k_band(const float2* __restrict__ x, float2* __restrict__ out,
+                                                  const float2* __restrict__ dcls, int L, int N, int r, float scale,
+                                                  double* __restrict__ dot_part) {
+  extern __shared__ __align__(16) float2 bsm[];
   __shared__ double red[8];
   const int R2 = 2 * r - 1, w = r - 1;
   const int strip = blockIdx.y;  // 0 top, 1 bottom, 2 left, 3 right
@@ -279,113 +280,99 @@ __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, floa
   const int d = lf / L, l = lf - d * L;
   const int horiz = strip < 2;
   const int lo = (strip == 0 || strip == 2);
-  const int nchunk = (N + BAND_TX - 1) / BAND_TX;
+  const int nchunk = (N - 2 * w + BAND_TX - 1) / BAND_TX;
   const int line = blockIdx.x / nchunk, chunk = blockIdx.x - line * nchunk;
   const int tid = threadIdx.x, j = tid >> 5, lane = tid & 31;
   const int nt = blockDim.x;
   const int Wl = BAND_TX + R2 - 1;
-  const int start = (horiz ? 0 : w) + chunk * BAND_TX;
-  const int limit = horiz ? N : N - w;
+  const int start = w + chunk * BAND_TX;  // first pixel along the line
+  const int limit = N - w;
   const int fixed = (lo ? 0 : N - w) + line;
   const size_t NN = (size_t)N * N;
   const float2* xl = x + (size_t)lf * NS * NN;
-  const size_t cls_stride = (size_t)NS * R2 * R2 * NS;
-  const float2* dl = dcls + (size_t)lf * R2 * R2 * cls_stride;
-  float2* xs = bsm;                              // [NS][R2][Wl]
-  float2* part = xs + (size_t)NS * R2 * Wl;      // [NS (j)][BAND_TX][NS (i)]
-  const bool active = start < limit;
-  if (active) {
-    for (int e = tid; e < NS * R2 * Wl; e += nt) {
-      const int jj = e / (R2 * Wl), rem = e - jj * R2 * Wl;
-      const int aa = rem / Wl, u = rem - aa * Wl;
-      int gy, gx;
-      if (horiz) {
-        gy = fixed + aa - w;
-        gx = start - w + u;
-      } else {
-        gy = start - w + u;
-        gx = fixed + aa - w;
-      }
+  const int ntap = NS * R2 * R2 * NS;  // taps of one class
+  const int cfix = lo ? line : r + line;  // class along the fixed coordinate
+  const int clsline = horiz ? cfix * R2 + (r - 1) : (r - 1) * R2 + cfix;
+  const float2* tl = dcls + ((size_t)lf * R2 * R2 + clsline) * ntap;
+  float2* tsm = bsm;                               // [NS (j)][R2*R2][NS (i)]
+  float2* xs = tsm + ((ntap + 1) & ~1);            // [NS][R2][Wl]
+  float2* part = xs;                               // [NS (j)][BAND_TX][NS (i)], after the window is used
+  for (int e = tid; e < ntap; e += nt) cp_async8(tsm + e, tl + e);
+  // window rows (shot jj, across aa): one warp per row, lanes along the line.  Along the
+  // line only [start - w, min(start + BAND_TX, limit) + w) is read by kept pixels: all of
+  // it inside the image (the rest of the row is never written and only feeds discarded
+  // pixels); across the line the window wraps periodically.
+  const int Wv = min(Wl, limit - start + 2 * w);
+  for (int row = j; row < NS * R2; row += nt >> 5) {
+    const int jj = row / R2, aa = row - jj * R2;
+    float2* dst = xs + (size_t)row * Wl;
+    if (horiz) {
+      int gy = fixed + aa - w;
       gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+      const float2* src = xl + (size_t)jj * NN + (size_t)gy * N + (start - w);
+      for (int u = lane; u < Wv; u += 32) cp_async8(dst + u, src + u);
+    } else {
+      int gx = fixed + aa - w;
       gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
-      xs[e] = xl[(size_t)jj * NN + (size_t)gy * N + gx];
+      const float2* src = xl + (size_t)jj * NN + (size_t)(start - w) * N + gx;
+      for (int u = lane; u < Wv; u += 32) cp_async8(dst + u, src + (size_t)u * N);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
-  const int cfix = lo ? line : r + line;  // class along the fixed coordinate
-  if (active) {
-    const int clsline = horiz ? cfix * R2 + (r - 1) : (r - 1) * R2 + cfix;
-    const int pu0 = lane * BAND_P;
-    float2 acc[BAND_P][NS];
+  float2 acc[BAND_P][NS];
 #pragma unroll
-    for (int p = 0; p < BAND_P; ++p)
+  for (int p = 0; p < BAND_P; ++p)
 #pragma unroll
-      for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
-    const float2* taps = dl + (size_t)clsline * cls_stride + (size_t)j * R2 * R2 * NS;
+    for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
+  {
+    const float2* taps = tsm + (size_t)j * R2 * R2 * NS;
     for (int aa = 0; aa < R2; ++aa) {
-      const float2* xr = xs + ((size_t)j * R2 + aa) * Wl + pu0;
-#pragma unroll 4
+      const float2* xr = xs + ((size_t)j * R2 + aa) * Wl + lane;
       for (int bb = 0; bb < R2; ++bb) {
         const int dd = horiz ? aa * R2 + bb : bb * R2 + aa;
         const float2* tp = taps + (size_t)dd * NS;
         float2 tv[NS];
-        if (NS % 2 == 0) {
+        if (NS % 2 == 0 && (ntap % 2 == 0)) {
 #pragma unroll
-          for (int i = 0; i < NS; i += 2) {
-            const float4 t4 = __ldg(reinterpret_cast<const float4*>(tp + i));
+          for (int i = 0; i + 1 < NS; i += 2) {
+            const float4 t4 = *reinterpret_cast<const float4*>(tp + i);
             tv[i] = cmk(t4.x, t4.y);
-            tv[i + 1 < NS ? i + 1 : i] = cmk(t4.z, t4.w);
+            tv[i + 1] = cmk(t4.z, t4.w);
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < NS; ++i) tv[i] = __ldg(tp + i);
+          for (int i = 0; i < NS; ++i) tv[i] = tp[i];
         }
 #pragma unroll
         for (int p = 0; p < BAND_P; ++p) {
-          const float2 xv = xr[p + bb];
+          const float2 xv = xr[32 * p + bb];
 #pragma unroll
           for (int i = 0; i < NS; ++i) cfma(acc[p][i], tv[i], xv);
         }
       }
     }
-#pragma unroll
-    for (int p = 0; p < BAND_P; ++p) {
-      const int pos = start + pu0 + p;
-      if (horiz && pos < N && (pos < w || pos > N - r)) {
-        // corner pixel: its own class along x
-        const int cx = pos < w ? pos : (r - 1) + (pos - (N - r));
-        const float2* ct = dl + (size_t)(cfix * R2 + cx) * cls_stride + (size_t)j * R2 * R2 * NS;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
-        for (int aa = 0; aa < R2; ++aa)
-          for (int bb = 0; bb < R2; ++bb) {
-            const float2 xv = xs[((size_t)j * R2 + aa) * Wl + pu0 + p + bb];
-            const float2* tp = ct + (size_t)(aa * R2 + bb) * NS;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) cfma(acc[p][i], tp[i], xv);
-          }
-      }
-#pragma unroll
-      for (int i = 0; i < NS; ++i) part[((size_t)j * BAND_TX + pu0 + p) * NS + i] = acc[p][i];
-    }
   }
+  __syncthreads();  // the window is no longer read: part takes its place
+#pragma unroll
+  for (int p = 0; p < BAND_P; ++p)
+#pragma unroll
+    for (int i = 0; i < NS; ++i) part[((size_t)j * BAND_TX + lane + 32 * p) * NS + i] = acc[p][i];
   __syncthreads();
   double dsum = 0.0;
-  if (active) {
-    for (int t = tid; t < BAND_TX * NS; t += nt) {
-      const int pu = t / NS, i = t - pu * NS;
-      const int pos = start + pu;
-      if (pos >= limit) continue;
-      float2 sacc = part[(size_t)pu * NS + i];
-      for (int jj = 1; jj < NS; ++jj) sacc = cadd(sacc, part[((size_t)jj * BAND_TX + pu) * NS + i]);
-      const int ny = horiz ? fixed : pos, nx = horiz ? pos : fixed;
-      const size_t o = ((size_t)lf * NS + i) * NN + (size_t)ny * N + nx;
-      const float2 c = cscale(sacc, scale);
-      out[o] = cadd(out[o], c);
-      if (dot_part) {
-        const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
-        dsum += (double)xv.x * c.x + (double)xv.y * c.y;
-      }
+  for (int t = tid; t < BAND_TX * NS; t += nt) {
+    const int pu = t / NS, i = t - pu * NS;
+    const int pos = start + pu;
+    if (pos >= limit) continue;
+    float2 sacc = part[(size_t)pu * NS + i];
+    for (int jj = 1; jj < NS; ++jj) sacc = cadd(sacc, part[((size_t)jj * BAND_TX + pu) * NS + i]);
+    const int ny = horiz ? fixed : pos, nx = horiz ? pos : fixed;
+    const size_t o = ((size_t)lf * NS + i) * NN + (size_t)ny * N + nx;
+    const float2 c = cscale(sacc, scale);
+    out[o] = cadd(out[o], c);
+    if (dot_part) {
+      const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
+      dsum += (double)xv.x * c.x + (double)xv.y * c.y;
     }
   }
   if (dot_part) {
@@ -400,14 +387,106 @@ __global__ void __launch_bounds__(256) k_band(const float2* __restrict__ x, floa
   }
 }
 
-static int band_chunks(const smsm_plan_s* P) { return (P->r - 1) * ((P->N + BAND_TX - 1) / BAND_TX); }
+// One CTA per (corner, flat (direction, slice)).  The corner's x window (3(r-1)
+// lines each way, periodically wrapped) of every shot is staged in shared
+// memory; thread (pixel, input shot j, output shot i) of the (r-1)^2 corner
+// pixels -- each with its own class -- sums the R2^2 taps of its class (read
+// from global memory, many loads in flight per thread), and the Ns partials
+// of each (pixel, i) are then added in a fixed order.
+#define BAND_CORNER_THREADS 512
+__global__ void __launch_bounds__(BAND_CORNER_THREADS) k_band_corner(const float2* __restrict__ x,
+                                                                     float2* __restrict__ out,
+                                                                     const float2* __restrict__ dcls, int L, int Ns,
+                                                                     int N, int r, float scale,
+                                                                     double* __restrict__ dot_part, int part_base) {
+  extern __shared__ __align__(16) float2 csm[];
+  __shared__ double red[BAND_CORNER_THREADS / 32];
+  const int R2 = 2 * r - 1, w = r - 1, W3 = 3 * w;
+  const int corner = blockIdx.x;  // bit 0: right, bit 1: bottom
+  const int lf = blockIdx.y;
+  const int d = lf / L, l = lf - d * L;
+  const size_t NN = (size_t)N * N;
+  const float2* xl = x + (size_t)lf * Ns * NN;
+  const int ntap = Ns * R2 * R2 * Ns;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int y0 = (corner & 2) ? N - w : 0, x0 = (corner & 1) ? N - w : 0;  // first corner pixel
+  float2* xw = csm;                          // [Ns][W3][W3]: pixel (y0 - w + a, x0 - w + b)
+  float2* part = xw + (size_t)Ns * W3 * W3;  // [w*w][Ns (j)][Ns (i)]
+  for (int e = tid; e < Ns * W3 * W3; e += nt) {
+    const int jj = e / (W3 * W3), rem = e - jj * W3 * W3;
+    const int a = rem / W3, b = rem - a * W3;
+    int gy = y0 - w + a, gx = x0 - w + b;
+    gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+    gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+    xw[e] = xl[(size_t)jj * NN + (size_t)gy * N + gx];
+  }
+  __syncthreads();
+  const int nwork = w * w * Ns * Ns;
+  for (int t = tid; t < nwork; t += nt) {
+    const int i = t % Ns, jj = (t / Ns) % Ns, pix = t / (Ns * Ns);
+    const int py = pix / w, px = pix - py * w;
+    const int cy = (corner & 2) ? r + py : py;
+    const int cx = (corner & 1) ? r + px : px;
+    const float2* ct = dcls + ((size_t)lf * R2 * R2 + cy * R2 + cx) * ntap + (size_t)jj * R2 * R2 * Ns + i;
+    const float2* xr = xw + (size_t)jj * W3 * W3 + py * W3 + px;  // tap (aa, bb) reads xr[aa*W3 + bb]
+    float2 s0 = cmk(0.f, 0.f), s1 = cmk(0.f, 0.f);
+    for (int aa = 0; aa < R2; ++aa) {
+      int bb = 0;
+      for (; bb + 1 < R2; bb += 2) {
+        const float2 t0 = __ldg(ct + (size_t)(aa * R2 + bb) * Ns);
+        const float2 t1 = __ldg(ct + (size_t)(aa * R2 + bb + 1) * Ns);
+        cfma(s0, t0, xr[aa * W3 + bb]);
+        cfma(s1, t1, xr[aa * W3 + bb + 1]);
+      }
+      if (bb < R2) cfma(s0, __ldg(ct + (size_t)(aa * R2 + bb) * Ns), xr[aa * W3 + bb]);
+    }
+    part[((size_t)pix * Ns + jj) * Ns + i] = cadd(s0, s1);
+  }
+  __syncthreads();
+  double dsum = 0.0;
+  for (int t = tid; t < w * w * Ns; t += nt) {
+    const int pix = t / Ns, i = t - pix * Ns;
+    const int py = pix / w, px = pix - py * w;
+    float2 sacc = part[(size_t)pix * Ns * Ns + i];
+    for (int jj = 1; jj < Ns; ++jj) sacc = cadd(sacc, part[((size_t)pix * Ns + jj) * Ns + i]);
+    const int ny = y0 + py, nx = x0 + px;
+    const size_t o = ((size_t)lf * Ns + i) * NN + (size_t)ny * N + nx;
+    const float2 c = cscale(sacc, scale);
+    out[o] = cadd(out[o], c);
+    if (dot_part) {
+      const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
+      dsum += (double)xv.x * c.x + (double)xv.y * c.y;
+    }
+  }
+  if (dot_part) {
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((tid & 31) == 0) red[tid >> 5] = dsum;
+    __syncthreads();
+    if (tid == 0) {
+      double sacc = 0.0;
+      for (int k = 0; k < (nt >> 5); ++k) sacc += red[k];
+      dot_part[(size_t)d * SMSM_PART_MAX + part_base + l * 4 + corner] = sacc;
+    }
+  }
+}
 
-// partial sums per direction written by k_band
-int band_blocks(const smsm_plan_s* P) { return P->r > 1 ? P->L * 4 * band_chunks(P) : 0; }
+static size_t band_corner_smem(const smsm_plan_s* P) {
+  const size_t w = P->r - 1, Ns = P->Ns;
+  return (Ns * 9 * w * w + w * w * Ns * Ns) * sizeof(float2);
+}
+
+static int band_chunks(const smsm_plan_s* P) {
+  return (P->r - 1) * ((P->N - 2 * (P->r - 1) + BAND_TX - 1) / BAND_TX);
+}
+
+// partial sums per direction written by k_band and k_band_corner
+int band_blocks(const smsm_plan_s* P) { return P->r > 1 ? P->L * 4 * band_chunks(P) + P->L * 4 : 0; }
 
 static size_t band_smem(const smsm_plan_s* P) {
-  const int R2 = P->R2;
-  return ((size_t)P->Ns * R2 * (BAND_TX + R2 - 1) + (size_t)P->Ns * BAND_TX * P->Ns) * sizeof(float2);
+  const int R2 = P->R2, Ns = P->Ns;
+  const size_t ntap = (size_t)Ns * R2 * R2 * Ns;
+  const size_t win = (size_t)Ns * R2 * (BAND_TX + R2 - 1), part = (size_t)Ns * BAND_TX * Ns;
+  return (((ntap + 1) & ~(size_t)1) + (win > part ? win : part)) * sizeof(float2);
 }
 
 typedef void (*BandFn)(const float2*, float2*, const float2*, int, int, int, float, double*);
@@ -426,7 +505,9 @@ static BandFn band_fn(const smsm_plan_s* P) {
 
 smsm_status band_init_attrs(const smsm_plan_s* P) {
   cudaError_t e = cudaFuncSetAttribute(band_fn(P), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess || band_smem(P) > 200 * 1024) {
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_band_corner, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess || band_smem(P) > 200 * 1024 || band_corner_smem(P) > 200 * 1024) {
     smsm_set_error("border-band kernel needs %zu bytes of shared memory", band_smem(P));
     return SMSM_ERR_ARG;
   }
@@ -442,5 +523,9 @@ smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, floa
   dim3 grid(band_chunks(P), 4, P->LD);
   band_fn(P)<<<grid, 32 * P->Ns, band_smem(P), s>>>(x, out, P->wcls, P->L, P->N, P->r, scale, dot_part);
   SMSM_LAUNCH_CHECK("k_band");
+  // corner pixels: disjoint from the strips, so the two kernels may run in either order
+  k_band_corner<<<dim3(4, P->LD), BAND_CORNER_THREADS, band_corner_smem(P), s>>>(
+      x, out, P->wcls, P->L, P->Ns, P->N, P->r, scale, dot_part, P->L * 4 * band_chunks(P));
+  SMSM_LAUNCH_CHECK("k_band_corner");
   return SMSM_OK;
 }

@@ -380,6 +380,7 @@ smsm_status launch_col(const smsm_plan_s* P, int mode, int with_phase, const flo
   a.sN = P->sN;
   a.lambda = lambda;
   a.dot_part = dot_part;
+  a.errflag = P->devflag;
   if (mode == COL_NORMAL && !with_phase && P->alias) return launch_col_alias(P, a, s);
   if (mode == COL_NORMAL && !with_phase && !(P->flags & SMSM_FLAG_GENERIC_KERNELS)) {
     smsm_status fst = launch_col_fast(P, a, s);
