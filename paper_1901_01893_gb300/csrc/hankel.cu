@@ -387,92 +387,81 @@ __global__ void __launch_bounds__(32 * NS) k_band(const float2* __restrict__ x, 
   }
 }
 
-// One CTA per (corner, flat (direction, slice)).  The corner's x window (3(r-1)
-// lines each way, periodically wrapped) of every shot is staged in shared
-// memory; thread (pixel, input shot j, output shot i) of the (r-1)^2 corner
-// pixels -- each with its own class -- sums the R2^2 taps of its class (read
-// from global memory, many loads in flight per thread), and the Ns partials
-// of each (pixel, i) are then added in a fixed order.
-#define BAND_CORNER_THREADS 512
+// One CTA per (corner pixel, corner, flat (direction, slice)): every corner
+// pixel has its own class, so the CTA stages that class's taps [j][d][i] and the
+// pixel's R2 x R2 window of every shot (periodically wrapped) with asynchronous
+// copies, all in flight at once.  Thread (i, j, c) sums the taps d = c (mod nc)
+// of input shot j for output shot i; the partials of output shot i are then
+// added in a fixed order.
+#define BAND_CORNER_THREADS 128
 __global__ void __launch_bounds__(BAND_CORNER_THREADS) k_band_corner(const float2* __restrict__ x,
                                                                      float2* __restrict__ out,
                                                                      const float2* __restrict__ dcls, int L, int Ns,
                                                                      int N, int r, float scale,
                                                                      double* __restrict__ dot_part, int part_base) {
   extern __shared__ __align__(16) float2 csm[];
-  __shared__ double red[BAND_CORNER_THREADS / 32];
-  const int R2 = 2 * r - 1, w = r - 1, W3 = 3 * w;
-  const int corner = blockIdx.x;  // bit 0: right, bit 1: bottom
-  const int lf = blockIdx.y;
+  const int R2 = 2 * r - 1, w = r - 1, RR = R2 * R2;
+  const int pix = blockIdx.x;     // py * w + px
+  const int corner = blockIdx.y;  // bit 0: right, bit 1: bottom
+  const int lf = blockIdx.z;
   const int d = lf / L, l = lf - d * L;
+  const int py = pix / w, px = pix - py * w;
+  const int ny = ((corner & 2) ? N - w : 0) + py, nx = ((corner & 1) ? N - w : 0) + px;
+  const int cy = (corner & 2) ? r + py : py, cx = (corner & 1) ? r + px : px;
   const size_t NN = (size_t)N * N;
   const float2* xl = x + (size_t)lf * Ns * NN;
-  const int ntap = Ns * R2 * R2 * Ns;
+  const int ntap = Ns * RR * Ns;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int y0 = (corner & 2) ? N - w : 0, x0 = (corner & 1) ? N - w : 0;  // first corner pixel
-  float2* xw = csm;                          // [Ns][W3][W3]: pixel (y0 - w + a, x0 - w + b)
-  float2* part = xw + (size_t)Ns * W3 * W3;  // [w*w][Ns (j)][Ns (i)]
-  for (int e = tid; e < Ns * W3 * W3; e += nt) {
-    const int jj = e / (W3 * W3), rem = e - jj * W3 * W3;
-    const int a = rem / W3, b = rem - a * W3;
-    int gy = y0 - w + a, gx = x0 - w + b;
+  float2* tsm = csm;                     // [Ns (j)][RR][Ns (i)]
+  float2* xw = tsm + ntap;               // [Ns][R2][R2]: pixel (ny + aa - w, nx + bb - w)
+  float2* part = xw + (size_t)Ns * RR;   // [Ns (i)][Ns (j) * nc]
+  const float2* ct = dcls + ((size_t)lf * RR + cy * R2 + cx) * ntap;
+  for (int e = tid; e < ntap; e += nt) cp_async8(tsm + e, ct + e);
+  for (int e = tid; e < Ns * RR; e += nt) {
+    const int jj = e / RR, rem = e - jj * RR;
+    const int aa = rem / R2, bb = rem - aa * R2;
+    int gy = ny + aa - w, gx = nx + bb - w;
     gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
     gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
-    xw[e] = xl[(size_t)jj * NN + (size_t)gy * N + gx];
+    cp_async8(xw + e, xl + (size_t)jj * NN + (size_t)gy * N + gx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int npair = Ns * Ns;
+  const int nc = nt / npair > 0 ? nt / npair : 1;  // tap subsets per (i, j)
+  for (int t = tid; t < npair * nc; t += nt) {
+    const int i = t % Ns, jj = (t / Ns) % Ns, c = t / npair;
+    const float2* tp = tsm + (size_t)jj * RR * Ns + i;
+    const float2* xr = xw + (size_t)jj * RR;
+    float2 s = cmk(0.f, 0.f);
+    for (int dd = c; dd < RR; dd += nc) cfma(s, tp[(size_t)dd * Ns], xr[dd]);
+    part[(size_t)i * Ns * nc + jj * nc + c] = s;
   }
   __syncthreads();
-  const int nwork = w * w * Ns * Ns;
-  for (int t = tid; t < nwork; t += nt) {
-    const int i = t % Ns, jj = (t / Ns) % Ns, pix = t / (Ns * Ns);
-    const int py = pix / w, px = pix - py * w;
-    const int cy = (corner & 2) ? r + py : py;
-    const int cx = (corner & 1) ? r + px : px;
-    const float2* ct = dcls + ((size_t)lf * R2 * R2 + cy * R2 + cx) * ntap + (size_t)jj * R2 * R2 * Ns + i;
-    const float2* xr = xw + (size_t)jj * W3 * W3 + py * W3 + px;  // tap (aa, bb) reads xr[aa*W3 + bb]
-    float2 s0 = cmk(0.f, 0.f), s1 = cmk(0.f, 0.f);
-    for (int aa = 0; aa < R2; ++aa) {
-      int bb = 0;
-      for (; bb + 1 < R2; bb += 2) {
-        const float2 t0 = __ldg(ct + (size_t)(aa * R2 + bb) * Ns);
-        const float2 t1 = __ldg(ct + (size_t)(aa * R2 + bb + 1) * Ns);
-        cfma(s0, t0, xr[aa * W3 + bb]);
-        cfma(s1, t1, xr[aa * W3 + bb + 1]);
+  if (tid < 32) {
+    double dsum = 0.0;
+    for (int i = tid; i < Ns; i += 32) {
+      float2 sacc = cmk(0.f, 0.f);
+      for (int k = 0; k < Ns * nc; ++k) sacc = cadd(sacc, part[(size_t)i * Ns * nc + k]);
+      const size_t o = ((size_t)lf * Ns + i) * NN + (size_t)ny * N + nx;
+      const float2 cc = cscale(sacc, scale);
+      out[o] = cadd(out[o], cc);
+      if (dot_part) {
+        const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
+        dsum += (double)xv.x * cc.x + (double)xv.y * cc.y;
       }
-      if (bb < R2) cfma(s0, __ldg(ct + (size_t)(aa * R2 + bb) * Ns), xr[aa * W3 + bb]);
     }
-    part[((size_t)pix * Ns + jj) * Ns + i] = cadd(s0, s1);
-  }
-  __syncthreads();
-  double dsum = 0.0;
-  for (int t = tid; t < w * w * Ns; t += nt) {
-    const int pix = t / Ns, i = t - pix * Ns;
-    const int py = pix / w, px = pix - py * w;
-    float2 sacc = part[(size_t)pix * Ns * Ns + i];
-    for (int jj = 1; jj < Ns; ++jj) sacc = cadd(sacc, part[((size_t)pix * Ns + jj) * Ns + i]);
-    const int ny = y0 + py, nx = x0 + px;
-    const size_t o = ((size_t)lf * Ns + i) * NN + (size_t)ny * N + nx;
-    const float2 c = cscale(sacc, scale);
-    out[o] = cadd(out[o], c);
     if (dot_part) {
-      const float2 xv = xl[(size_t)i * NN + (size_t)ny * N + nx];
-      dsum += (double)xv.x * c.x + (double)xv.y * c.y;
-    }
-  }
-  if (dot_part) {
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-    if ((tid & 31) == 0) red[tid >> 5] = dsum;
-    __syncthreads();
-    if (tid == 0) {
-      double sacc = 0.0;
-      for (int k = 0; k < (nt >> 5); ++k) sacc += red[k];
-      dot_part[(size_t)d * SMSM_PART_MAX + part_base + l * 4 + corner] = sacc;
+      for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      if (tid == 0) dot_part[(size_t)d * SMSM_PART_MAX + part_base + ((size_t)l * 4 + corner) * w * w + pix] = dsum;
     }
   }
 }
 
 static size_t band_corner_smem(const smsm_plan_s* P) {
-  const size_t w = P->r - 1, Ns = P->Ns;
-  return (Ns * 9 * w * w + w * w * Ns * Ns) * sizeof(float2);
+  const size_t R2 = P->R2, Ns = P->Ns;
+  const size_t npair = Ns * Ns, nc = BAND_CORNER_THREADS / npair > 0 ? BAND_CORNER_THREADS / npair : 1;
+  return (Ns * R2 * R2 * Ns + Ns * R2 * R2 + npair * nc) * sizeof(float2);
 }
 
 static int band_chunks(const smsm_plan_s* P) {
@@ -480,7 +469,9 @@ static int band_chunks(const smsm_plan_s* P) {
 }
 
 // partial sums per direction written by k_band and k_band_corner
-int band_blocks(const smsm_plan_s* P) { return P->r > 1 ? P->L * 4 * band_chunks(P) + P->L * 4 : 0; }
+int band_blocks(const smsm_plan_s* P) {
+  return P->r > 1 ? P->L * 4 * band_chunks(P) + P->L * 4 * (P->r - 1) * (P->r - 1) : 0;
+}
 
 static size_t band_smem(const smsm_plan_s* P) {
   const int R2 = P->R2, Ns = P->Ns;
@@ -524,7 +515,7 @@ smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, floa
   band_fn(P)<<<grid, 32 * P->Ns, band_smem(P), s>>>(x, out, P->wcls, P->L, P->N, P->r, scale, dot_part);
   SMSM_LAUNCH_CHECK("k_band");
   // corner pixels: disjoint from the strips, so the two kernels may run in either order
-  k_band_corner<<<dim3(4, P->LD), BAND_CORNER_THREADS, band_corner_smem(P), s>>>(
+  k_band_corner<<<dim3((P->r - 1) * (P->r - 1), 4, P->LD), BAND_CORNER_THREADS, band_corner_smem(P), s>>>(
       x, out, P->wcls, P->L, P->Ns, P->N, P->r, scale, dot_part, P->L * 4 * band_chunks(P));
   SMSM_LAUNCH_CHECK("k_band_corner");
   return SMSM_OK;
