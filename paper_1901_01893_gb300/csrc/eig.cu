@@ -39,14 +39,39 @@ __device__ __forceinline__ void jpair(int round, int k, int Cp, int& p, int& q) 
 
 __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z == 1.f && J.w == 0.f; }
 
+// Rotation k of a round acts on the pair (p_k, q_k) with
 // J = [[c, s], [-s e, c e]],  e = exp(-i phi) = (er, ei), phi = arg(G_pq).
 // G lives in shared memory with row stride Cp+1 (odd, so column walks hit
 // distinct banks).  Each round: C/2 threads compute the rotations of the
 // round-robin pairs (p_k, q_k) into shared tables; then every 2x2 block
 // (k1 <= k2) is transformed as J_k1^H B J_k2, its mirror (k2, k1) written as
 // the conjugate transpose (G stays exactly Hermitian), and the diagonal blocks
-// are set to their analytic result diag(a - t|b|, d + t|b|).
+// are set to their analytic result diag(a - t|b|, d + t|b|).  The blocks of
+// the triangle k1 <= k2 < n (n = Cp/2, rounded up to even) are dealt out
+// evenly: rows k and n-1-k of the triangle together hold n+1 blocks, so the
+// triangle is an (n/2) x (n+1) rectangle of block indices.
 // warm != 0: start from Gw = V_prev^H G V_prev (symmetrised on load).
+
+// block bi of the folded triangle -> (k1, k2), k1 <= k2 < n (n even)
+__device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, int& k2) {
+  int fr = __float2int_rz(((float)bi + 0.5f) * inv_n1);
+  int c = bi - fr * (n + 1);
+  if (c < 0) {
+    --fr;
+    c += n + 1;
+  } else if (c > n) {
+    ++fr;
+    c -= n + 1;
+  }
+  if (c < n - fr) {
+    k1 = fr;
+    k2 = fr + c;
+  } else {
+    k1 = n - 1 - fr;
+    k2 = k1 + (c - (n - fr));
+  }
+}
+
 __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, const float2* __restrict__ Gw,
                                                  float* __restrict__ eig, float4* __restrict__ rlog,
                                                  int* __restrict__ sweeps_out, int C, int Cp, int max_sweeps,
@@ -54,13 +79,14 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   extern __shared__ float2 g[];
   const int ld = Cp + 1;
   const int half = Cp / 2;
+  const int nh = (half + 1) & ~1;  // triangle edge rounded up to even (virtual pair skipped)
+  const int nblk = (nh / 2) * (nh + 1);
+  const float inv_n1 = 1.f / (float)(nh + 1);
   float4* rot = reinterpret_cast<float4*>(g + (size_t)Cp * ld + ((Cp * ld) & 1));
   int* rp = reinterpret_cast<int*>(rot + half);
   int* rq = rp + half;
-  __shared__ int nrot;
   __shared__ float dmax;
   const int l = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   const double2* Gl = G + (size_t)l * C * C;
   const float2* Gwl = Gw ? Gw + (size_t)l * C * C : nullptr;
   for (int e = tid; e < Cp * Cp; e += nt) {
@@ -85,8 +111,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   const float floor_abs = 1e-7f * dmax;
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
-    if (tid == 0) nrot = 0;
-    __syncthreads();
+    int rotated = 0;  // this thread set a non-identity rotation during the sweep
     for (int round = 0; round < Cp - 1; ++round) {
       if (tid < half) {
         int p, q;
@@ -102,75 +127,82 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
           const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
           const float c = 1.f / sqrtf(t * t + 1.f);
           J = make_float4(c, t * c, b.x / babs, -b.y / babs);
-          atomicAdd(&nrot, 1);
+          rotated = 1;
         }
         rot[tid] = J;
         rlog[(((size_t)l * SMSM_MAX_SWEEPS + sw) * (Cp - 1) + round) * half + tid] = J;
       }
       __syncthreads();
-      for (int k1 = warp; k1 < half; k1 += nwarp) {
+      for (int bi = tid; bi < nblk; bi += nt) {
+        int k1, k2;
+        tri_block(bi, nh, inv_n1, k1, k2);
+        if (k2 >= half) continue;  // virtual pair of an odd half
         const float4 J1 = rot[k1];
         const bool id1 = is_ident(J1);
         const int p1 = rp[k1], q1 = rq[k1];
-        const float2 e1c = cmk(J1.z, -J1.w);
-        for (int k2 = k1 + lane; k2 < half; k2 += 32) {
-          const float4 J2 = rot[k2];
-          if (k2 == k1) {
-            if (id1) continue;
-            const float a = g[p1 * ld + p1].x, d = g[q1 * ld + q1].x;
-            const float2 b = g[p1 * ld + q1];
-            const float tb = (J1.y / J1.x) * hypotf(b.x, b.y);
-            g[p1 * ld + p1] = cmk(a - tb, 0.f);
-            g[q1 * ld + q1] = cmk(d + tb, 0.f);
-            g[p1 * ld + q1] = cmk(0.f, 0.f);
-            g[q1 * ld + p1] = cmk(0.f, 0.f);
-            continue;
-          }
-          if (id1 && is_ident(J2)) continue;
-          const int p2 = rp[k2], q2 = rq[k2];
-          const float2 B00 = g[p1 * ld + p2], B01 = g[p1 * ld + q2];
-          const float2 B10 = g[q1 * ld + p2], B11 = g[q1 * ld + q2];
-          // T = J1^H B : row0 = c B0 - s conj(e1) B1 ; row1 = s B0 + c conj(e1) B1
-          const float2 T00 = csub(cscale(B00, J1.x), cscale(cmul(e1c, B10), J1.y));
-          const float2 T01 = csub(cscale(B01, J1.x), cscale(cmul(e1c, B11), J1.y));
-          const float2 T10 = cadd(cscale(B00, J1.y), cscale(cmul(e1c, B10), J1.x));
-          const float2 T11 = cadd(cscale(B01, J1.y), cscale(cmul(e1c, B11), J1.x));
-          // O = T J2 : col0 = c T0 - s e2 T1 ; col1 = s T0 + c e2 T1
-          const float2 e2 = cmk(J2.z, J2.w);
-          const float2 O00 = csub(cscale(T00, J2.x), cscale(cmul(T01, e2), J2.y));
-          const float2 O10 = csub(cscale(T10, J2.x), cscale(cmul(T11, e2), J2.y));
-          const float2 O01 = cadd(cscale(T00, J2.y), cscale(cmul(T01, e2), J2.x));
-          const float2 O11 = cadd(cscale(T10, J2.y), cscale(cmul(T11, e2), J2.x));
-          g[p1 * ld + p2] = O00;
-          g[p1 * ld + q2] = O01;
-          g[q1 * ld + p2] = O10;
-          g[q1 * ld + q2] = O11;
-          g[p2 * ld + p1] = conjf2(O00);
-          g[q2 * ld + p1] = conjf2(O01);
-          g[p2 * ld + q1] = conjf2(O10);
-          g[q2 * ld + q1] = conjf2(O11);
+        if (k2 == k1) {
+          if (id1) continue;
+          const float a = g[p1 * ld + p1].x, d = g[q1 * ld + q1].x;
+          const float2 b = g[p1 * ld + q1];
+          const float tb = (J1.y / J1.x) * hypotf(b.x, b.y);
+          g[p1 * ld + p1] = cmk(a - tb, 0.f);
+          g[q1 * ld + q1] = cmk(d + tb, 0.f);
+          g[p1 * ld + q1] = cmk(0.f, 0.f);
+          g[q1 * ld + p1] = cmk(0.f, 0.f);
+          continue;
         }
+        const float4 J2 = rot[k2];
+        if (id1 && is_ident(J2)) continue;
+        const int p2 = rp[k2], q2 = rq[k2];
+        const float2 B00 = g[p1 * ld + p2], B01 = g[p1 * ld + q2];
+        // row q1 times conj(e1)
+        const float2 e1c = cmk(J1.z, -J1.w);
+        const float2 B10 = cmul(e1c, g[q1 * ld + p2]), B11 = cmul(e1c, g[q1 * ld + q2]);
+        // T = J1^H B : row0 = c B0 - s B1', row1 = s B0 + c B1'
+        const float c1 = J1.x, s1 = J1.y;
+        const float2 T00 = cmk(c1 * B00.x - s1 * B10.x, c1 * B00.y - s1 * B10.y);
+        const float2 T01 = cmk(c1 * B01.x - s1 * B11.x, c1 * B01.y - s1 * B11.y);
+        const float2 T10 = cmk(s1 * B00.x + c1 * B10.x, s1 * B00.y + c1 * B10.y);
+        const float2 T11 = cmk(s1 * B01.x + c1 * B11.x, s1 * B01.y + c1 * B11.y);
+        // O = T J2 : col0 = c T0 - s T1', col1 = s T0 + c T1', T1' = e2 T1
+        const float2 e2 = cmk(J2.z, J2.w);
+        const float2 U01 = cmul(T01, e2), U11 = cmul(T11, e2);
+        const float c2 = J2.x, s2 = J2.y;
+        const float2 O00 = cmk(c2 * T00.x - s2 * U01.x, c2 * T00.y - s2 * U01.y);
+        const float2 O10 = cmk(c2 * T10.x - s2 * U11.x, c2 * T10.y - s2 * U11.y);
+        const float2 O01 = cmk(s2 * T00.x + c2 * U01.x, s2 * T00.y + c2 * U01.y);
+        const float2 O11 = cmk(s2 * T10.x + c2 * U11.x, s2 * T10.y + c2 * U11.y);
+        g[p1 * ld + p2] = O00;
+        g[p1 * ld + q2] = O01;
+        g[q1 * ld + p2] = O10;
+        g[q1 * ld + q2] = O11;
+        g[p2 * ld + p1] = conjf2(O00);
+        g[q2 * ld + p1] = conjf2(O01);
+        g[p2 * ld + q1] = conjf2(O10);
+        g[q2 * ld + q1] = conjf2(O11);
       }
       __syncthreads();
     }
-    const bool done = (nrot == 0);
-    __syncthreads();
-    if (done) break;
+    if (!__syncthreads_or(rotated)) break;
   }
   for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
 }
 
 // V = V0 * (product of the logged rotations), V0 = I or the previous V (warm).
-// One CTA per (matrix, 32 rows); each warp owns 4 rows in shared memory and
-// applies every round's rotations to them, reading each rotation once.
-#define VA_ROWS_PER_WARP 4
+// One CTA per (matrix, 8 VA_ROWS_PER_WARP rows); each warp owns VA_ROWS_PER_WARP
+// rows in shared memory and applies every round's rotations to them.  Lane j
+// handles the pairs k = j + 32 u; their indices advance by one (mod Cp-1) from
+// round to round, and the next round's rotations are loaded while the current
+// ones are applied.
+#define VA_ROWS_PER_WARP 8
+#define VA_SLOTS 6  // pair slots per lane: Cp/2 <= 32 VA_SLOTS
 __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog, const int* __restrict__ sweeps,
                                                 float2* __restrict__ V, int C, int Cp, int warm) {
   extern __shared__ float2 rows[];
   const int l = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t0 = blockIdx.y * 32 + w * VA_ROWS_PER_WARP;
+  const int t0 = (blockIdx.y * 8 + w) * VA_ROWS_PER_WARP;
   float2* myrows = rows + (size_t)w * VA_ROWS_PER_WARP * Cp;
   float2* Vl = V + (size_t)l * C * C;
 #pragma unroll
@@ -184,27 +216,71 @@ __global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog,
   }
   __syncwarp();
   const int nsw = sweeps[l];
-  const int half = Cp / 2;
-  for (int sw = 0; sw < nsw; ++sw) {
-    for (int round = 0; round < Cp - 1; ++round) {
-      const float4* lg = rlog + (((size_t)l * SMSM_MAX_SWEEPS + sw) * (Cp - 1) + round) * half;
-      for (int k = lane; k < half; k += 32) {
-        const float4 J = lg[k];
-        if (is_ident(J)) continue;
-        int p, q;
-        jpair(round, k, Cp, p, q);
-        const float2 e = cmk(J.z, J.w);
+  const int half = Cp / 2, m = Cp - 1;
+  const int nround = nsw * m;
+  const float4* lg0 = rlog + (size_t)l * SMSM_MAX_SWEEPS * m * half;
+  // round-robin state of slot u (pair k = lane + 32u): jpair with ia = (k + round) % m,
+  // ib = (m - k + round) % m, advanced by one each round
+  int ia[VA_SLOTS], ib[VA_SLOTS];
+#pragma unroll
+  for (int u = 0; u < VA_SLOTS; ++u) {
+    const int k = lane + 32 * u;
+    ia[u] = k % m;
+    ib[u] = (m - k % m) % m;
+  }
+  float4 Jn[VA_SLOTS];
+#pragma unroll
+  for (int u = 0; u < VA_SLOTS; ++u) {
+    const int k = lane + 32 * u;
+    Jn[u] = (k < half && nround > 0) ? __ldg(lg0 + k) : make_float4(1.f, 0.f, 1.f, 0.f);
+  }
+  for (int gr = 0; gr < nround; ++gr) {
+    const int round = gr % m;  // rounds of a sweep are logged contiguously, sweeps follow each other
+    if (round == 0) {
+#pragma unroll
+      for (int u = 0; u < VA_SLOTS; ++u) {
+        const int k = lane + 32 * u;
+        ia[u] = k % m;
+        ib[u] = (m - k % m) % m;
+      }
+    }
+    float4 J[VA_SLOTS];
+#pragma unroll
+    for (int u = 0; u < VA_SLOTS; ++u) J[u] = Jn[u];
+    if (gr + 1 < nround) {
+      const float4* lg = lg0 + (size_t)(gr + 1) * half;
+#pragma unroll
+      for (int u = 0; u < VA_SLOTS; ++u) {
+        const int k = lane + 32 * u;
+        if (k < half) Jn[u] = __ldg(lg + k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < VA_SLOTS; ++u) {
+      const int k = lane + 32 * u;
+      if (k < half && !is_ident(J[u])) {
+        int a, b;
+        if (k == 0) {
+          a = 0;
+          b = 1 + round;
+        } else {
+          a = 1 + ia[u];
+          b = 1 + ib[u];
+        }
+        const int p = min(a, b), q = max(a, b);
+        const float2 e = cmk(J[u].z, J[u].w);
 #pragma unroll
         for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
           float2* row = myrows + rr * Cp;
-          const float2 vp = row[p], vq = row[q];
-          const float2 evq = cmul(e, vq);
-          row[p] = csub(cscale(vp, J.x), cscale(evq, J.y));
-          row[q] = cadd(cscale(vp, J.y), cscale(evq, J.x));
+          const float2 vp = row[p], evq = cmul(e, row[q]);
+          row[p] = cmk(J[u].x * vp.x - J[u].y * evq.x, J[u].x * vp.y - J[u].y * evq.y);
+          row[q] = cmk(J[u].y * vp.x + J[u].x * evq.x, J[u].y * vp.y + J[u].x * evq.y);
         }
       }
-      __syncwarp();
+      ia[u] = ia[u] + 1 == m ? 0 : ia[u] + 1;
+      ib[u] = ib[u] + 1 == m ? 0 : ib[u] + 1;
     }
+    __syncwarp();
   }
 #pragma unroll
   for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
@@ -336,6 +412,12 @@ smsm_status eig_init_attrs(int Cp) {
     smsm_set_error("Jacobi kernel cannot get %zu bytes of shared memory: %s", sm, cudaGetErrorString(e));
     return SMSM_ERR_ARG;
   }
+  const size_t vsm = (size_t)8 * VA_ROWS_PER_WARP * Cp * sizeof(float2);
+  e = cudaFuncSetAttribute(k_vapply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+  if (e != cudaSuccess) {
+    smsm_set_error("rotation replay kernel cannot get %zu bytes of shared memory: %s", vsm, cudaGetErrorString(e));
+    return SMSM_ERR_ARG;
+  }
   return SMSM_OK;
 }
 
@@ -361,7 +443,7 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  dim3 gv(P->LD, (C + 31) / 32);
+  dim3 gv(P->LD, (C + 8 * VA_ROWS_PER_WARP - 1) / (8 * VA_ROWS_PER_WARP));
   k_vapply<<<gv, 256, (size_t)8 * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
                                                                               warm);
   SMSM_LAUNCH_CHECK("k_vapply");
