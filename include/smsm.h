@@ -113,8 +113,16 @@ typedef struct {
                          events inside the solve and report their device time */
   int eig_cold;       /* 1: restart the eigensolver from scratch every outer iteration
                          (default 0: start from the previous iteration's eigenvectors) */
-  int reserved[4];
+  int lanes;          /* batch > 1: split the batch into this many sub-batches solved as
+                         concurrent branches of the captured graph, started out of phase
+                         so that one lane's (latency-bound) eigensolver runs while other
+                         lanes' CG runs; 0 -> automatic (3 for a batch of at least 9, 2
+                         from 4), at most SMSM_MAX_LANES and the batch.  Results do not
+                         depend on it. */
+  int reserved[3];
 } smsm_params;
+
+#define SMSM_MAX_LANES 4
 
 #define SMSM_MAX_OUTER 128
 
@@ -146,8 +154,11 @@ typedef struct {
   int sweeps[SMSM_MAX_OUTER];           /* Jacobi sweeps used (max over slices) */
   float elapsed_ms;                     /* device time of the solve (CUDA events) */
   int graph_kernels;                    /* kernel launches in one solve (nodes of its graph) */
-  float stage_ms[16];                   /* device time per smsm_stage (timed stages only) */
+  float stage_ms[16];                   /* device time per smsm_stage (timed stages only; with
+                                           several lanes, the launches of lane 0) */
   int stage_launches[16];               /* timed launches per smsm_stage */
+  int lanes;                            /* concurrent lanes the batch was solved as */
+  int lane0_batch;                      /* problems in lane 0 (each timed launch covers them) */
 } smsm_report;
 
 /* Fill *p with the defaults listed above. */

@@ -102,6 +102,10 @@ static void free_plan(smsm_plan_s* P) {
   if (P->has_graph) cudaGraphExecDestroy(P->gexec);
   solver_free_timing(P);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  for (int k = 0; k < SMSM_MAX_LANES; ++k)
+    if (P->lane_s[k]) cudaStreamDestroy(P->lane_s[k]);
+  for (int k = 0; k < 2 * SMSM_MAX_LANES + 1; ++k)
+    if (P->lane_ev[k]) cudaEventDestroy(P->lane_ev[k]);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   free(P);
@@ -239,12 +243,13 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     A(ash, (size_t)shots * shots);
   }
   A(devflag, 1);
-  A(rep, 1);
+  A(rep, SMSM_MAX_LANES);  // one report record per lane; lane 0's is the one returned
 #undef A
   if (st) {
     free_plan(P);
     return st;
   }
+  P->nvb = vec_blocks(P);  // fixed for the plan: lanes (sub-batches) reduce in the same order
   if (band_blocks(P) > SMSM_PART_MAX || vec_blocks(P) > SMSM_PART_MAX) {
     free_plan(P);
     smsm_set_error("smsm_plan: problem too large for the partial-sum buffers");
@@ -317,6 +322,10 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   }
   if (!st) {
     cudaError_t e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    for (int k = 1; k < SMSM_MAX_LANES && e == cudaSuccess; ++k)
+      e = cudaStreamCreateWithFlags(&P->lane_s[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 2 * SMSM_MAX_LANES + 1 && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&P->lane_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&P->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&P->ev1);
     if (e == cudaSuccess) e = cudaMemset(P->part_pq_band, 0, sizeof(double) * SMSM_PART_MAX * D);
@@ -505,9 +514,10 @@ extern "C" smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x
   if (p.outer_iters < 0 || p.outer_iters > SMSM_MAX_OUTER || p.cg_iters < 0 || p.eta < 1.0 ||
       !(p.lambda >= 0.0) || !(p.eps0_rel > 0.0) || !(p.eps_min_rel > 0.0) ||
       (p.mode != SMSM_MODE_IRLS && p.mode != SMSM_MODE_NULLSPACE) ||
-      (p.mode == SMSM_MODE_NULLSPACE && (p.rank <= 0 || p.rank >= plan->C))) {
+      (p.mode == SMSM_MODE_NULLSPACE && (p.rank <= 0 || p.rank >= plan->C)) || p.lanes < 0 ||
+      p.lanes > SMSM_MAX_LANES) {
     smsm_set_error("smsm_reconstruct: invalid parameters (K in [0,%d], J >= 0, eta >= 1, lambda >= 0, "
-                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C))", SMSM_MAX_OUTER);
+                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C), lanes in [0, %d])", SMSM_MAX_OUTER, SMSM_MAX_LANES);
     return SMSM_ERR_ARG;
   }
   return solver_reconstruct(plan, y, x, &p, report, S(stream));

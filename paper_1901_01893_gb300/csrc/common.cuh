@@ -95,6 +95,7 @@ struct smsm_plan_s {
   float2* ash;    // [Ns][Ns]: exp(-2 pi j (i - N/2) q / Ns)
   int* devflag;   // device error flag raised by bounded waits (SMSM_ERR_TIMEOUT)
   int LD;  // D * L: number of (direction, slice) Hankel matrices
+  int nvb; // CTAs per direction of the CG vector kernels (fixed at plan creation)
   int nband;  // pixels within r-1 of an edge
   int dev;
   FftDesc fN, fM;
@@ -128,6 +129,8 @@ struct smsm_plan_s {
   // graph cache for smsm_reconstruct
   cudaGraphExec_t gexec;
   cudaStream_t cap_stream;
+  cudaStream_t lane_s[SMSM_MAX_LANES];  // capture streams of lanes 1.. (lane 0 captures on cap_stream)
+  cudaEvent_t lane_ev[2 * SMSM_MAX_LANES + 1];  // fork, per-lane join and eigen-step events
   smsm_params gparams;
   int has_graph;
   int graph_kernels;

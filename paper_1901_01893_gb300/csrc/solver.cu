@@ -24,8 +24,10 @@ void solver_free_timing(smsm_plan_s* P) {
 
 #define VEC_THREADS 256
 
-// CTAs per direction of the CG vector kernels
+// CTAs per direction of the CG vector kernels (chosen once per plan from the whole batch,
+// so a sub-batch view splits its reductions the same way)
 int vec_blocks(const smsm_plan_s* P) {
+  if (P->nvb > 0) return P->nvb;
   const size_t n2 = (size_t)P->L * P->Ns * P->N * P->N / 2;  // float4 = two complex
   size_t b = (n2 + VEC_THREADS - 1) / VEC_THREADS;
   size_t cap = (size_t)(4 * 152 + P->D - 1) / P->D;
@@ -212,7 +214,74 @@ smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float l
   return normal_pen_timed(P, v, q, lambda, with_dots, s, nullptr);
 }
 
-static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s) {
+// The plan restricted to directions [d0, d0 + nd): same geometry, tables and
+// coil data; every per-direction buffer offset to the sub-batch; its own report
+// record and CG scalar banks.  Used to solve sub-batches as concurrent lanes.
+static smsm_plan_s lane_view(const smsm_plan_s* P, int d0, int nd, int lane) {
+  smsm_plan_s v = *P;
+  const size_t L = P->L, Ns = P->Ns, NN = (size_t)P->N * P->N, C = P->C, Cp = P->Cp, R2 = P->R2;
+  const size_t B = L * Ns, dd = (size_t)d0;
+  v.D = nd;
+  v.LD = nd * P->L;
+  const size_t vec = dd * B * NN;
+  v.hA += vec;
+  v.hB += vec;
+  v.phaseT += vec;
+  v.xs += vec;
+  v.bv += vec;
+  v.rv += vec;
+  v.pv += vec;
+  v.qv += vec;
+  const size_t yv = dd * Ns * P->Nc * P->M * P->N;
+  v.yh += yv;
+  v.ybuf += yv;
+  const size_t cc = dd * L * C * C;
+  v.G64 += cc;
+  v.V += cc;
+  v.Wf += cc;
+  v.Gw += cc;
+  v.Gw2 += cc;
+  v.Gpart += cc * P->gram_nkx;
+  v.eig += dd * L * Cp;
+  v.rotlog += dd * L * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2);
+  v.sweeps += dd * L;
+  v.wper += dd * L * Ns * Ns * R2 * R2;
+  v.wcls += dd * L * R2 * R2 * Ns * Ns * R2 * R2;
+  v.multT += dd * L * Ns * Ns * NN;
+  v.part_pq_col += dd * SMSM_PART_MAX;
+  v.part_pq_band += dd * SMSM_PART_MAX;
+  v.part_rr += 2 * dd * SMSM_PART_MAX;
+  v.st += dd;
+  v.rep = P->rep + lane;
+  if (P->Rpart) {
+    const size_t R2C = 2 * (size_t)gram_tc_cp(P);
+    v.Rpart += dd * L * P->gram_tc_nG * R2C * R2C;
+  }
+  return v;
+}
+
+// b = A^H y and the starting point
+static smsm_status enqueue_prologue(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s, Timer* T) {
+  smsm_status st;
+  const int B = P->L * P->Ns;
+  const int D = P->D;
+  k_reset_state<<<1, 128, 0, s>>>(P->st, D);
+  SMSM_LAUNCH_CHECK("k_reset_state");
+  T->begin(SMSM_STAGE_ADJOINT);
+  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, D * P->Ns * P->Nc, P->M, 1, s))) return st;
+  if ((st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s))) return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, D * B, P->N, 0, s))) return st;
+  T->end(SMSM_STAGE_ADJOINT);
+  if (!prm->warm)
+    SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)D * B * P->N * P->N,
+                                  cudaMemcpyDeviceToDevice, s));
+  return SMSM_OK;
+}
+
+// Outer iteration k: Gram, eigen step and weights (after `eig_wait` when given;
+// `eig_done` recorded after them when given), filters, J CG steps.
+static smsm_status enqueue_outer(smsm_plan_s* P, const smsm_params* prm, int k, cudaStream_t s, Timer* T,
+                                 cudaEvent_t eig_wait, cudaEvent_t eig_done) {
   smsm_status st;
   const int B = P->L * P->Ns;
   const int D = P->D;
@@ -223,52 +292,91 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
   double* rr0 = P->part_rr;
   double* rr1 = P->part_rr + (size_t)SMSM_PART_MAX * D;
   const dim3 vg(nvb, D);
+  T->begin(SMSM_STAGE_GRAM);
+  if ((st = launch_gram(P, P->xs, P->G64, s))) return st;
+  T->end(SMSM_STAGE_GRAM);
+  if (eig_wait) SMSM_CUDA_TRY(cudaStreamWaitEvent(s, eig_wait, 0));
+  if ((st = launch_eig_weights(P, P->G64, k, prm, s, T))) return st;
+  if (eig_done) SMSM_CUDA_TRY(cudaEventRecord(eig_done, s));
+  T->begin(SMSM_STAGE_FILTERS);
+  if ((st = launch_filters(P, P->Wf, s))) return st;
+  T->end(SMSM_STAGE_FILTERS);
+  if ((st = normal_pen_timed(P, P->xs, P->qv, lam, 0, s, T))) return st;
+  T->begin(SMSM_STAGE_CG);
+  k_cg_init<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv, (float4*)P->pv,
+                                        n4, rr0);
+  SMSM_LAUNCH_CHECK("k_cg_init");
+  T->end(SMSM_STAGE_CG);
+  k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 0, rr0, nvb);
+  SMSM_LAUNCH_CHECK("k_record");
+  for (int j = 0; j < prm->cg_iters; ++j) {
+    double* rin = (j & 1) ? rr1 : rr0;
+    double* rout = (j & 1) ? rr0 : rr1;
+    if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, T))) return st;
+    T->begin(SMSM_STAGE_CG);
+    k_cg_update<<<vg, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
+                                            (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
+                                            lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
+    SMSM_LAUNCH_CHECK("k_cg_update");
+    k_cg_pupdate<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
+    SMSM_LAUNCH_CHECK("k_cg_pupdate");
+    T->end(SMSM_STAGE_CG);
+  }
+  double* rend = (prm->cg_iters & 1) ? rr1 : rr0;  // bank of the last write
+  k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 1, rend, nvb);
+  SMSM_LAUNCH_CHECK("k_record");
+  return SMSM_OK;
+}
+
+// lanes actually used for these parameters
+static int solve_lanes(const smsm_plan_s* P, const smsm_params* prm) {
+  int n = prm->lanes > 0 ? prm->lanes : (P->D >= 9 ? 3 : (P->D >= 4 ? 2 : 1));
+  if (n > SMSM_MAX_LANES) n = SMSM_MAX_LANES;
+  if (n > P->D) n = P->D;
+  return n < 1 ? 1 : n;
+}
+
+// The whole solve on stream s (being captured).  Stage timing brackets the
+// launches of lane 0 (its own stream).  With several lanes, lane k solves
+// directions [k D / n, (k+1) D / n) on its own stream, and lane k's first eigen
+// step waits for lane k-1's: the lanes start out of phase, so one lane's
+// eigensolver (a few CTAs that wait on latency) runs next to the other lanes'
+// bandwidth-bound kernels.  (Forcing the eigen steps to alternate for the whole
+// solve measured slower with three or more lanes: it serialises them.)
+static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStream_t s) {
+  smsm_status st;
   if (prm->timing && !P->tpool) P->tpool = new TimingPool();
   if (P->tpool) ((TimingPool*)P->tpool)->used = 0;
   Timer T{(TimingPool*)P->tpool, prm->timing, s};
-  k_reset_state<<<1, 128, 0, s>>>(P->st, D);
-  SMSM_LAUNCH_CHECK("k_reset_state");
-  // b = A^H y
-  T.begin(SMSM_STAGE_ADJOINT);
-  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, D * P->Ns * P->Nc, P->M, 1, s))) return st;
-  if ((st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s))) return st;
-  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, D * B, P->N, 0, s))) return st;
-  T.end(SMSM_STAGE_ADJOINT);
-  if (!prm->warm)
-    SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, P->bv, sizeof(float2) * (size_t)D * B * P->N * P->N,
-                                  cudaMemcpyDeviceToDevice, s));
-  for (int k = 0; k < prm->outer_iters; ++k) {
-    T.begin(SMSM_STAGE_GRAM);
-    if ((st = launch_gram(P, P->xs, P->G64, s))) return st;
-    T.end(SMSM_STAGE_GRAM);
-    if ((st = launch_eig_weights(P, P->G64, k, prm, s, &T))) return st;
-    T.begin(SMSM_STAGE_FILTERS);
-    if ((st = launch_filters(P, P->Wf, s))) return st;
-    T.end(SMSM_STAGE_FILTERS);
-    if ((st = normal_pen_timed(P, P->xs, P->qv, lam, 0, s, &T))) return st;
-    T.begin(SMSM_STAGE_CG);
-    k_cg_init<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv,
-                                          (float4*)P->pv, n4, rr0);
-    SMSM_LAUNCH_CHECK("k_cg_init");
-    T.end(SMSM_STAGE_CG);
-    k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 0, rr0, nvb);
-    SMSM_LAUNCH_CHECK("k_record");
-    for (int j = 0; j < prm->cg_iters; ++j) {
-      double* rin = (j & 1) ? rr1 : rr0;
-      double* rout = (j & 1) ? rr0 : rr1;
-      if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, &T))) return st;
-      T.begin(SMSM_STAGE_CG);
-      k_cg_update<<<vg, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
-                                              (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
-                                              lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
-      SMSM_LAUNCH_CHECK("k_cg_update");
-      k_cg_pupdate<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
-      SMSM_LAUNCH_CHECK("k_cg_pupdate");
-      T.end(SMSM_STAGE_CG);
+  Timer T0{nullptr, 0, s};
+  const int nl = solve_lanes(P, prm);
+  if (nl == 1) {
+    if ((st = enqueue_prologue(P, prm, s, &T))) return st;
+    for (int k = 0; k < prm->outer_iters; ++k)
+      if ((st = enqueue_outer(P, prm, k, s, &T, nullptr, nullptr))) return st;
+  } else {
+    smsm_plan_s view[SMSM_MAX_LANES];
+    cudaStream_t ls[SMSM_MAX_LANES];
+    cudaEvent_t fork = P->lane_ev[0];
+    cudaEvent_t* join = P->lane_ev + 1;                   // [nl]
+    cudaEvent_t* eigd = P->lane_ev + 1 + SMSM_MAX_LANES;  // [nl]
+    SMSM_CUDA_TRY(cudaEventRecord(fork, s));
+    for (int k = 0; k < nl; ++k) {
+      const int d0 = (int)((long)k * P->D / nl), d1 = (int)((long)(k + 1) * P->D / nl);
+      view[k] = lane_view(P, d0, d1 - d0, k);
+      ls[k] = k == 0 ? s : P->lane_s[k];
+      if (k) SMSM_CUDA_TRY(cudaStreamWaitEvent(ls[k], fork, 0));
+      if ((st = enqueue_prologue(&view[k], prm, ls[k], k ? &T0 : &T))) return st;
     }
-    double* rend = (prm->cg_iters & 1) ? rr1 : rr0;  // bank of the last write
-    k_record<<<1, VEC_THREADS, 0, s>>>(P->rep, k, 1, rend, nvb);
-    SMSM_LAUNCH_CHECK("k_record");
+    for (int j = 0; j < prm->outer_iters; ++j)
+      for (int k = 0; k < nl; ++k) {
+        cudaEvent_t wait = (k && j == 0) ? eigd[k - 1] : nullptr;
+        if ((st = enqueue_outer(&view[k], prm, j, ls[k], k ? &T0 : &T, wait, eigd[k]))) return st;
+      }
+    for (int k = 1; k < nl; ++k) {
+      SMSM_CUDA_TRY(cudaEventRecord(join[k], ls[k]));
+      SMSM_CUDA_TRY(cudaStreamWaitEvent(s, join[k], 0));
+    }
   }
   if (T.err != cudaSuccess) {
     smsm_set_error("timing events: %s", cudaGetErrorString(T.err));
@@ -344,6 +452,8 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
     float ms = 0.f;
     SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
     report->elapsed_ms = ms;
+    report->lanes = solve_lanes(P, prm);
+    report->lane0_batch = P->D / report->lanes;
     report->graph_kernels = P->graph_kernels;
     TimingPool* tp = (TimingPool*)P->tpool;
     if (tp && prm->timing) {

@@ -37,7 +37,7 @@ class Params(ctypes.Structure):
                 ("eps_min_rel", ctypes.c_double), ("outer_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("rank", ctypes.c_int), ("warm", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("timing", ctypes.c_int), ("eig_cold", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("lanes", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Report(ctypes.Structure):
@@ -45,7 +45,8 @@ class Report(ctypes.Structure):
                 ("eps", ctypes.c_double * SMSM_MAX_OUTER), ("rr_start", ctypes.c_double * SMSM_MAX_OUTER),
                 ("rr_end", ctypes.c_double * SMSM_MAX_OUTER), ("sweeps", ctypes.c_int * SMSM_MAX_OUTER),
                 ("elapsed_ms", ctypes.c_float), ("graph_kernels", ctypes.c_int),
-                ("stage_ms", ctypes.c_float * 16), ("stage_launches", ctypes.c_int * 16)]
+                ("stage_ms", ctypes.c_float * 16), ("stage_launches", ctypes.c_int * 16),
+                ("lanes", ctypes.c_int), ("lane0_batch", ctypes.c_int)]
 
 
 class SmsmError(RuntimeError):

@@ -281,6 +281,28 @@ def test_batch_matches_single_problems(smsm):
     assert O.nrmse(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
 
 
+def test_lanes_give_identical_results(smsm):
+    # Solving the batch as 1, 2 or 3 concurrent lanes (sub-batches on their own
+    # graph branches) changes the schedule only: every direction runs the same
+    # kernels with the same reduction splits, so the results are bit-identical.
+    key = "tiny"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    D = 5
+    g, xt, y0 = _problem(key, 6)
+    rng = np.random.default_rng(31)
+    ys = np.stack([y0 * np.exp(1j * 0.2 * d) + 0.05 * crandn(rng, *y0.shape) for d in range(D)])
+    p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    p.set_sens(c64(g["sens"]))
+    outs = []
+    for lanes in (1, 2, 3):
+        prm = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4, lanes=lanes)
+        x, rep = p.reconstruct(c64(ys), params=prm)
+        assert rep.status == 0
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("L,Ns,Nc,N,r,Ldiv", [
     (2, 4, 8, 64, 5, 0),    # M = 16 (lane segments)
     (3, 4, 6, 64, 3, 8),    # CAIPI shift N/8: classes pair pixels 8 apart within M = 16
