@@ -154,45 +154,85 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
 //   A tap (dy, dx) is in range for class (cy, cx) when the pixel plus the tap
 //   stays inside [0, N): dy >= -cy for low classes, dy <= 2r-2-cy for high ones.
 // ---------------------------------------------------------------------------
-__global__ void k_filters(const float2* __restrict__ W, float2* __restrict__ dcls, float2* __restrict__ wper, int Ns,
-                          int r, int C) {
-  const int R2 = 2 * r - 1;
-  const int cls = blockIdx.x;  // 0..R2*R2 (last = periodic filter)
-  const int ij = blockIdx.y;
-  const int l = blockIdx.z;
-  const int i = ij / Ns, j = ij - i * Ns;
-  const bool per = (cls == R2 * R2);
-  const int cy = per ? r - 1 : cls / R2, cx = per ? r - 1 : cls % R2;
-  const float2* Wl = W + (size_t)l * C * C;
+// One CTA per (input shot j, matrix l): the rows (j, q) of W_l are staged in
+// shared memory (row stride C+1); thread (d, i) forms, for its tap d and output
+// shot i, the r x r array A[p] = W[(j, p+d), (i, p)] (0 where p+d leaves the
+// support) and every class sum from running sums.  The valid-patch range of a
+// class is a prefix [0, c] or a suffix [c-r+1, r-1] of p along each axis, so
+// accumulating rows from the top (prefix classes) or from the bottom (suffix
+// classes) and, within the rows accumulated so far, column prefix and suffix
+// sums gives each class sum as one lookup.  The periodic filter is the full sum.
+#define FILT_MAXR 12
+__device__ __forceinline__ float2 filt_a(const float2* wi, int ldw, int r, int dy, int dx, int py, int px) {
+  const int qy = py + dy, qx = px + dx;
+  return (qy >= 0 && qy < r && qx >= 0 && qx < r) ? wi[(qy * r + qx) * ldw + py * r + px] : cmk(0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, float2* __restrict__ dcls,
+                                                 float2* __restrict__ wper, int Ns, int r, int C) {
+  extern __shared__ float2 sW[];  // [r*r (q)][C + 1]
+  const int R2 = 2 * r - 1, RR = R2 * R2;
+  const int j = blockIdx.x;
+  const int l = blockIdx.y;
   const int rr = r * r;
-  for (int d = threadIdx.x; d < R2 * R2; d += blockDim.x) {
+  const int ldw = C + 1;
+  const float2* Wl = W + (size_t)l * C * C + (size_t)j * rr * C;
+  for (int e = threadIdx.x; e < rr * C; e += blockDim.x) {
+    const int q = e / C, c = e - q * C;
+    sW[q * ldw + c] = Wl[e];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < RR * Ns; t += blockDim.x) {
+    const int i = t % Ns, d = t / Ns;
     const int dy = d / R2 - (r - 1), dx = d % R2 - (r - 1);
-    // periodic filter: all p with q = p + d in the filter support
+    const float2* wi = sW + i * rr;
+    // periodic filter: the sum over every p
     float2 sp = cmk(0.f, 0.f);
-    float2 sc = cmk(0.f, 0.f);
-    const int ly = max(0, cy - (r - 1)), hy = min(r - 1, cy);
-    const int lx = max(0, cx - (r - 1)), hx = min(r - 1, cx);
-    for (int py = 0; py < r; ++py) {
-      const int qy = py + dy;
-      if (qy < 0 || qy >= r) continue;
-      for (int px = 0; px < r; ++px) {
-        const int qx = px + dx;
-        if (qx < 0 || qx >= r) continue;
-        const float2 w = Wl[(size_t)(j * rr + qy * r + qx) * C + (i * rr + py * r + px)];
-        sp = cadd(sp, w);
-        if (py >= ly && py <= hy && px >= lx && px <= hx) sc = cadd(sc, w);
+    for (int py = 0; py < r; ++py)
+      for (int px = 0; px < r; ++px) sp = cadd(sp, filt_a(wi, ldw, r, dy, dx, py, px));
+    wper[((size_t)(l * Ns + i) * Ns + j) * RR + d] = sp;
+    float2* out = dcls + ((size_t)l * RR * Ns + j) * RR * Ns + (size_t)d * Ns + i;  // + cls * Ns * RR * Ns
+    const size_t cstride = (size_t)Ns * RR * Ns;
+    // pass 0: rows 0..cy (classes cy <= r-1); pass 1: rows cy-r+1..r-1 (classes cy >= r-1)
+    for (int pass = 0; pass < 2; ++pass) {
+      float2 cpre[FILT_MAXR], csuf[FILT_MAXR];  // column prefix / suffix sums over the rows so far
+#pragma unroll
+      for (int k = 0; k < FILT_MAXR; ++k) cpre[k] = csuf[k] = cmk(0.f, 0.f);
+      for (int step = 0; step < r; ++step) {
+        const int py = pass == 0 ? step : r - 1 - step;
+        float2 run = cmk(0.f, 0.f);
+#pragma unroll
+        for (int px = 0; px < FILT_MAXR; ++px)
+          if (px < r) {
+            run = cadd(run, filt_a(wi, ldw, r, dy, dx, py, px));
+            cpre[px] = cadd(cpre[px], run);
+          }
+        run = cmk(0.f, 0.f);
+#pragma unroll
+        for (int k = FILT_MAXR - 1; k >= 0; --k)
+          if (k < r) {
+            run = cadd(run, filt_a(wi, ldw, r, dy, dx, py, k));
+            csuf[k] = cadd(csuf[k], run);
+          }
+        // rows so far: [0, step] (pass 0: class cy = step) or [r-1-step, r-1] (pass 1:
+        // class cy = 2r-2-step, whose valid rows are [cy-r+1, r-1])
+        const int cy = pass == 0 ? step : 2 * r - 2 - step;
+        if (pass == 1 && step == r - 1) continue;  // cy = r-1 (all rows) came out of pass 0
+        const bool iny = (cy < r - 1) ? (dy >= -cy) : (cy > r - 1 ? dy <= 2 * r - 2 - cy : true);
+#pragma unroll
+        for (int cx = 0; cx < 2 * FILT_MAXR - 1; ++cx)
+          if (cx < R2) {
+            // columns [0, cx] (cx <= r-1) or [cx-r+1, r-1] (cx >= r-1)
+            const float2 sc = cx <= r - 1 ? cpre[cx < FILT_MAXR ? cx : 0] : csuf[cx - r + 1 < FILT_MAXR ? cx - r + 1 : 0];
+            const bool inx = (cx < r - 1) ? (dx >= -cx) : (cx > r - 1 ? dx <= 2 * r - 2 - cx : true);
+            out[(size_t)(cy * R2 + cx) * cstride] = (iny && inx) ? csub(sc, sp) : cscale(sp, -1.f);
+          }
       }
-    }
-    if (per) {
-      wper[((size_t)(l * Ns + i) * Ns + j) * R2 * R2 + d] = sp;
-    } else {
-      const bool iny = (cy < r - 1) ? (dy >= -cy) : (cy > r - 1 ? dy <= 2 * r - 2 - cy : true);
-      const bool inx = (cx < r - 1) ? (dx >= -cx) : (cx > r - 1 ? dx <= 2 * r - 2 - cx : true);
-      const float2 v = (iny && inx) ? csub(sc, sp) : cscale(sp, -1.f);
-      dcls[((((size_t)l * R2 * R2 + cls) * Ns + j) * R2 * R2 + d) * Ns + i] = v;
     }
   }
 }
+
+static size_t filters_smem(const smsm_plan_s* P) { return (size_t)P->r * P->r * (P->C + 1) * sizeof(float2); }
 
 // multT[l][i][i'][x][y] = sum_dy E[dy][y] sum_dx wt[dy][dx] E[dx][x],  E[d][n] = exp(-j 2 pi (d-(r-1)) (n - N/2)/N)
 #define MULT_XB 8
@@ -236,9 +276,8 @@ smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2*
 }
 
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s) {
-  const int R2 = P->R2;
-  dim3 g1(R2 * R2 + 1, P->Ns * P->Ns, P->LD);
-  k_filters<<<g1, 128, 0, s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C);  // wcls holds the class taps dcls
+  k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, P->wcls, P->wper, P->Ns, P->r,
+                                                              P->C);  // wcls holds the class taps dcls
   SMSM_LAUNCH_CHECK("k_filters");
   dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->LD);
   k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
@@ -498,7 +537,9 @@ smsm_status band_init_attrs(const smsm_plan_s* P) {
   cudaError_t e = cudaFuncSetAttribute(band_fn(P), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_band_corner, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess || band_smem(P) > 200 * 1024 || band_corner_smem(P) > 200 * 1024) {
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filters, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess || band_smem(P) > 200 * 1024 || band_corner_smem(P) > 200 * 1024 ||
+      filters_smem(P) > 200 * 1024) {
     smsm_set_error("border-band kernel needs %zu bytes of shared memory", band_smem(P));
     return SMSM_ERR_ARG;
   }
