@@ -63,8 +63,10 @@ __device__ void block_partial(double v, double* red, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
-__device__ __forceinline__ double norm2_4(float4 v) {
-  return (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+// squared norm of a float4, accumulated in FP32: a thread sums only a few dozen of
+// them before its partial goes on in FP64 (FP64 arithmetic is scarce on this part)
+__device__ __forceinline__ float norm2_4(float4 v, float acc) {
+  return fmaf(v.w, v.w, fmaf(v.z, v.z, fmaf(v.y, v.y, fmaf(v.x, v.x, acc))));
 }
 
 // Vectors are [D][n4] float4 (direction d = blockIdx.y); partial arrays are
@@ -84,15 +86,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_init(const float4* __restric
   q += off_;
   r += off_;
   p += off_;
-  double s = 0.0;
+  float s = 0.f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
     float4 bv = b[e], qv = q[e];
     float4 rv = make_float4(bv.x - qv.x, bv.y - qv.y, bv.z - qv.z, bv.w - qv.w);
     r[e] = rv;
     p[e] = rv;
-    s += norm2_4(rv);
+    s = norm2_4(rv, s);
   }
-  block_partial(s, red, part_rr + poff_);
+  block_partial((double)s, red, part_rr + poff_);
 }
 
 // alpha = <r,r>/<p,q>; x += alpha p; r -= alpha q; partial ||r||^2
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ 
     alpha = 0.0;
   }
   const float a = (float)alpha;
-  double s = 0.0;
+  float s = 0.f;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
     float4 xv = x[e], rv = r[e];
     const float4 pv = p[e], qv = q[e];
@@ -131,9 +133,9 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ 
     rv.w = fmaf(-a, qv.w, rv.w);
     x[e] = xv;
     r[e] = rv;
-    s += norm2_4(rv);
+    s = norm2_4(rv, s);
   }
-  block_partial(s, red, rr_out + poff_);
+  block_partial((double)s, red, rr_out + poff_);
 }
 
 // beta = rr_new/rr_old; p = r + beta p
