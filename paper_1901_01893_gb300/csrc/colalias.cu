@@ -24,17 +24,18 @@
 #include "fft.cuh"
 #include "umma.cuh"
 
-// sC[x][z][a][a'] = sum_c conj(S_{c,l}(x, y_a)) S_{c,l'}(x, y_a'), FP64 accumulation
+// corr[x][a][a'][z] = sum_c conj(S_{c,l}(x, y_a)) S_{c,l'}(x, y_a'), FP64 accumulation
+// (class z fastest: the threads of a warp, consecutive pixels y, read consecutive classes)
 __global__ void k_alias_corr(const float2* __restrict__ sensT, float2* __restrict__ corr, int L, int Ns, int Nc,
                              int N, int M, int sh) {
   const int B = L * Ns;
   const size_t NN = (size_t)N * N;
   const size_t total = (size_t)N * M * B * B;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int ap = (int)(e % B);
-    const int a = (int)((e / B) % B);
-    const int z = (int)((e / ((size_t)B * B)) % M);
-    const int x = (int)(e / ((size_t)B * B * M));
+    const int z = (int)(e % M);
+    const int ap = (int)((e / M) % B);
+    const int a = (int)((e / ((size_t)M * B)) % B);
+    const int x = (int)(e / ((size_t)M * B * B));
     const int l = a / Ns, t = a - l * Ns, lp = ap / Ns, tp = ap - lp * Ns;
     const int y = (z - (l * sh) % M + M) % M + t * M;
     const int yp = (z - (lp * sh) % M + M) % M + tp * M;
@@ -172,10 +173,10 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     float2 c[B];  // row (l, t) of this pixel's class matrix, shared by every shot
-    const float2* crow = cx + ((size_t)zl[l] * B + (l * NS + t)) * B;
+    const float2* crow = cx + (size_t)(l * NS + t) * B * M + zl[l];
     if (own) {
 #pragma unroll
-      for (int ap = 0; ap < B; ++ap) c[ap] = __ldg(crow + ap);
+      for (int ap = 0; ap < B; ++ap) c[ap] = __ldg(crow + (size_t)ap * M);
     }
     int i0 = (bsub - l * NS) % tpy;
     if (i0 < 0) i0 += tpy;

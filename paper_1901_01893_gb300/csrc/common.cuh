@@ -91,7 +91,7 @@ struct smsm_plan_s {
   int gram_tc_nG; // split-K partials of the tensor-core Gram
   float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials
   int alias;      // 1: column stage of A^H A through the per-class coil correlations
-  float2* acorr;  // [N(x)][M(class)][L Ns][L Ns] coil correlations of the aliasing classes
+  float2* acorr;  // [N(x)][L Ns][L Ns][M(class)] coil correlations of the aliasing classes
   float2* ash;    // [Ns][Ns]: exp(-2 pi j (i - N/2) q / Ns)
   int* devflag;   // device error flag raised by bounded waits (SMSM_ERR_TIMEOUT)
   int LD;  // D * L: number of (direction, slice) Hankel matrices
