@@ -9,12 +9,16 @@ Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
 * caipi_ramp ................ pinned (integer shift == circular image roll)
 * forward / adjoint ......... pinned (dense DFT-matrix brute force at N=8,
                               adjoint dot test, A = I special case)
-* hankel / hankel_adjoint ... pinned (entrywise definition, dot test)
-* gram ...................... pinned (trace closed form, PSD, rank bounds)
+* hankel / hankel_adjoint ... pinned (entrywise definition, dot test; the
+                              periodic variant likewise)
+* gram ...................... pinned (trace closed form, PSD, rank bounds;
+                              periodic: circular cross-correlation by FFTs)
 * irls_weight ............... pinned (W^2 (G + eps I) = I)
 * nullspace_weight .......... pinned (projector, annihilates a low-rank H)
 * penalty ................... pinned (brute-force sum, W = I closed form,
-                              periodic-FFT agreement on interior pixels)
+                              periodic-FFT agreement on interior pixels;
+                              periodic boundary: W = I and FFT agreement
+                              at every pixel)
 * cg ........................ pinned (exact solve in n steps, small SPD)
 * reconstruct ............... pinned (exact recovery with full sampling;
                               slice-phase equivariance; noiseless recovery)

@@ -21,6 +21,8 @@ Conventions (readings of the paper, where it is silent or garbled):
   per slice).  Ldiv defaults to L (an FOV/L shift).
 * Hankel lifting (Eq. 8): rows are the VALID patch origins k in [0, N-r]^2
   (row-major), columns (i, py, px) -> i*r*r + py*r + px, entry x_i[k + p].
+  The PERIODIC variant (``periodic=True``) takes every origin k in [0, N)^2
+  with the entry x_i[(k + p) mod N] (k-space treated as periodic).
 * Solver: the paper minimises Eq. 10 with an augmented-Lagrangian scheme
   whose pseudo-code lives in another paper; here the same cost is minimised
   by iteratively reweighted least squares (IRLS): the nuclear norm is
@@ -138,34 +140,45 @@ def normal(x: np.ndarray, sens: np.ndarray, Ldiv: int | None = None) -> np.ndarr
 # ---------------------------------------------------------------------------
 
 
-def hankel(xl: np.ndarray, r: int) -> np.ndarray:
+def hankel(xl: np.ndarray, r: int, periodic: bool = False) -> np.ndarray:
     """Block Hankel matrix H_l = [H(x_{l,1}) ... H(x_{l,Ns})] of Eq. 9.
 
-    xl : [Ns][N][N]; returns [(N-r+1)^2][Ns*r*r] with entry x_i[k + p].
+    xl : [Ns][N][N]; returns [(N-r+1)^2][Ns*r*r] with entry x_i[k + p]
+    (periodic: [N^2][Ns*r*r] with entry x_i[(k + p) mod N]).
     """
     Ns, N, _ = xl.shape
+    if periodic:
+        # wrap the first r-1 rows and columns around, then the VALID windows of
+        # the extended image are exactly the N^2 periodic patches
+        xl = np.concatenate([xl, xl[:, : r - 1, :]], axis=1)
+        xl = np.concatenate([xl, xl[:, :, : r - 1]], axis=2)
     win = np.lib.stride_tricks.sliding_window_view(xl, (r, r), axis=(1, 2))
     # win[i, ky, kx, py, px] = xl[i, ky+py, kx+px]
-    P = (N - r + 1) ** 2
-    return np.ascontiguousarray(win.transpose(1, 2, 0, 3, 4)).reshape(P, Ns * r * r)
+    V = N if periodic else N - r + 1
+    return np.ascontiguousarray(win.transpose(1, 2, 0, 3, 4)).reshape(V * V, Ns * r * r)
 
 
-def hankel_adjoint(Y: np.ndarray, Ns: int, N: int, r: int) -> np.ndarray:
-    """H^*(Y): every entry Y[k, (i,p)] goes back to pixel k + p of shot i."""
-    V = N - r + 1
+def hankel_adjoint(Y: np.ndarray, Ns: int, N: int, r: int, periodic: bool = False) -> np.ndarray:
+    """H^*(Y): every entry Y[k, (i,p)] goes back to pixel k + p (mod N when
+    periodic) of shot i."""
+    V = N if periodic else N - r + 1
     Yr = Y.reshape(V, V, Ns, r, r)
     out = np.zeros((Ns, N, N), dtype=np.complex128)
     for py in range(r):
         for px in range(r):
-            out[:, py:py + V, px:px + V] += Yr[:, :, :, py, px].transpose(2, 0, 1)
+            blk = Yr[:, :, :, py, px].transpose(2, 0, 1)
+            if periodic:
+                out += np.roll(blk, (py, px), axis=(1, 2))
+            else:
+                out[:, py:py + V, px:px + V] += blk
     return out
 
 
-def gram(x: np.ndarray, r: int) -> np.ndarray:
+def gram(x: np.ndarray, r: int, periodic: bool = False) -> np.ndarray:
     """G_l = H_l^H H_l for every slice: [L][C][C], C = Ns*r*r."""
     out = []
     for l in range(x.shape[0]):
-        H = hankel(x[l], r)
+        H = hankel(x[l], r, periodic)
         out.append(H.conj().T @ H)
     return np.stack(out)
 
@@ -197,13 +210,13 @@ def nullspace_weight(G: np.ndarray, rank: int) -> tuple[np.ndarray, np.ndarray]:
     return np.stack(Ws), np.stack(ss)
 
 
-def penalty(x: np.ndarray, W: np.ndarray, r: int) -> np.ndarray:
+def penalty(x: np.ndarray, W: np.ndarray, r: int, periodic: bool = False) -> np.ndarray:
     """P_W(x)_l = H_l^*(H_l(x_l) W_l): the gradient (up to 2) of ||H_l(x) W^(1/2)||_F^2."""
     L, Ns, N, _ = x.shape
     out = np.empty_like(x, dtype=np.complex128)
     for l in range(L):
-        H = hankel(x[l], r)
-        out[l] = hankel_adjoint(H @ W[l], Ns, N, r)
+        H = hankel(x[l], r, periodic)
+        out[l] = hankel_adjoint(H @ W[l], Ns, N, r, periodic)
     return out
 
 
@@ -241,7 +254,7 @@ def cg(apply_N, b: np.ndarray, x: np.ndarray, J: int) -> tuple[np.ndarray, list[
 # ---------------------------------------------------------------------------
 
 DEFAULT_PARAMS = dict(lam=1e-2, eps0_rel=1e-2, eta=1.5, eps_min_rel=1e-4, K=10, J=10,
-                      mode="irls", rank=0)
+                      mode="irls", rank=0, periodic=False)
 
 
 def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = None,
@@ -264,8 +277,9 @@ def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = N
     x = b.copy() if x0 is None else np.array(x0, dtype=np.complex128)
     eps = eps_min = None
     hist = []
+    per = bool(p["periodic"])
     for k in range(p["K"]):
-        G = gram(x, r)
+        G = gram(x, r, per)
         if p["mode"] == "nullspace":
             W, s = nullspace_weight(G, p["rank"])
         else:
@@ -279,7 +293,7 @@ def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = N
         lam = p["lam"]
 
         def apply_N(v, W=W):
-            return normal(v, sens, Ldiv) + lam * penalty(v, W, r)
+            return normal(v, sens, Ldiv) + lam * penalty(v, W, r, per)
 
         x, h = cg(apply_N, b, x, p["J"])
         hist.append(dict(eps=eps, rr=h))

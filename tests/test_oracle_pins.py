@@ -268,6 +268,65 @@ def test_penalty_interior_equals_periodic_fft_convolution():
     assert np.allclose(got[..., sl, sl], ref[..., sl, sl], atol=1e-10)
 
 
+# --- PERIODIC boundary (every origin k in [0, N)^2, indices mod N) -------------
+
+def test_periodic_hankel_entries_and_adjoint():
+    Ns, N, r = 2, 7, 3
+    x = crandn(Ns, N, N)
+    H = O.hankel(x, r, periodic=True)
+    assert H.shape == (N * N, Ns * r * r)
+    for _ in range(60):
+        ky, kx = RNG.integers(0, N, 2)
+        i, py, px = RNG.integers(0, Ns), *RNG.integers(0, r, 2)
+        assert H[ky * N + kx, i * r * r + py * r + px] == x[i, (ky + py) % N, (kx + px) % N]
+    Y = crandn(*H.shape)
+    lhs = O.vdot(H, Y)
+    rhs = O.vdot(x, O.hankel_adjoint(Y, Ns, N, r, periodic=True))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_periodic_gram_is_circular_cross_correlation():
+    # Every origin is used, so G[(i,p),(j,q)] = sum_k conj(x_i[k]) x_j[k + q - p]: the
+    # circular cross-correlation of shots i and j at lag q - p, here by the correlation
+    # theorem (FFTs) -- a route that never forms H.
+    L, Ns, N, r = 1, 2, 8, 3
+    x = crandn(L, Ns, N, N)
+    G = O.gram(x, r, periodic=True)[0]
+    F = [np.fft.fft2(x[0, i]) for i in range(Ns)]
+    for i in range(Ns):
+        for j in range(Ns):
+            c = np.fft.ifft2(np.conj(F[i]) * F[j])  # c[d] = sum_k conj(x_i[k]) x_j[k + d]
+            for py in range(r):
+                for px in range(r):
+                    for qy in range(r):
+                        for qx in range(r):
+                            ref = c[(qy - py) % N, (qx - px) % N]
+                            got = G[i * r * r + py * r + px, j * r * r + qy * r + qx]
+                            assert abs(got - ref) <= 1e-10 * np.abs(c).max()
+
+
+def test_periodic_penalty_identity_weight_and_fft_convolution():
+    L, Ns, N, r = 1, 2, 9, 3
+    x = crandn(L, Ns, N, N)
+    C = Ns * r * r
+    # W = I: every pixel lies in exactly r*r periodic patches
+    assert np.allclose(O.penalty(x, np.eye(C)[None], r, periodic=True), r * r * x, atol=1e-12)
+    # general W: the multichannel correlation holds at every pixel (no border band)
+    W = _random_hermitian(L, C)
+    ref = np.zeros_like(x)
+    for i in range(Ns):
+        for j in range(Ns):
+            K = np.zeros((N, N), dtype=complex)
+            for py in range(r):
+                for px in range(r):
+                    for qy in range(r):
+                        for qx in range(r):
+                            K[(-(qy - py)) % N, (-(qx - px)) % N] += W[0, j * r * r + qy * r + qx,
+                                                                      i * r * r + py * r + px]
+            ref[0, i] += np.fft.ifft2(np.fft.fft2(K) * np.fft.fft2(x[0, j]))
+    assert np.allclose(O.penalty(x, W, r, periodic=True), ref, atol=1e-10)
+
+
 # --- CG ------------------------------------------------------------------------
 
 def test_cg_solves_small_hpd_system_exactly():
