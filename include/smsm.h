@@ -67,7 +67,8 @@ typedef struct {
   int batch;       /* D, number of problems per call; 0 -> 1 (at most 4096) */
   int flags;       /* SMSM_FLAG_* bits */
   int precision;   /* smsm_precision of the Hankel Gram (default FP32) */
-  int reserved[4];
+  int boundary;    /* smsm_boundary of the Hankel lifting (default VALID) */
+  int reserved[3];
 } smsm_opts;
 
 /*
@@ -78,6 +79,13 @@ typedef struct {
  *   BF16_SPLIT: the same with BF16 hi and lo (~2^-16 relative per product).
  */
 typedef enum { SMSM_PRECISION_FP32 = 0, SMSM_PRECISION_BF16_SPLIT = 1 } smsm_precision;
+
+/* smsm_opts.boundary: which patch origins the Hankel lifting of Eq. 8 takes.
+ *   VALID: k in [0, N-r]^2, the (N1-r+1)(N2-r+1) rows of Eq. 8;
+ *   PERIODIC: every k in [0, N)^2 with indices taken mod N (k-space treated as
+ *             periodic).  Then the Gram is block circular cross-correlation and the
+ *             penalty is the image-domain multiplier alone (no border band). */
+typedef enum { SMSM_BOUNDARY_VALID = 0, SMSM_BOUNDARY_PERIODIC = 1 } smsm_boundary;
 
 /* smsm_opts.flags (same results up to rounding; for testing and comparison):
  *   GENERIC_KERNELS: the shape-generic kernels even where a specialised fast

@@ -175,6 +175,13 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     smsm_set_error("smsm_plan: unknown precision %d", opts->precision);
     return SMSM_ERR_ARG;
   }
+  const int boundary = opts ? opts->boundary : SMSM_BOUNDARY_VALID;
+  if (boundary != SMSM_BOUNDARY_VALID && boundary != SMSM_BOUNDARY_PERIODIC) {
+    free(P);
+    smsm_set_error("smsm_plan: unknown boundary %d", boundary);
+    return SMSM_ERR_ARG;
+  }
+  P->periodic = boundary == SMSM_BOUNDARY_PERIODIC;
   P->gram_tc = gram_tc_supported(P) && !(P->flags & SMSM_FLAG_GENERIC_KERNELS);
   if (P->precision == SMSM_PRECISION_BF16_SPLIT && !gram_tc_supported(P)) {
     free(P);
@@ -183,13 +190,13 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   }
   if (P->precision == SMSM_PRECISION_BF16_SPLIT) P->gram_tc = 1;
   P->alias = !(P->flags & (SMSM_FLAG_GENERIC_KERNELS | SMSM_FLAG_PER_COIL_NORMAL)) && alias_supported(P);
-  P->P1 = N - r + 1;
+  P->P1 = P->periodic ? N : N - r + 1;
   P->R2 = 2 * r - 1;
   P->fN = fN;
   P->fM = fM;
   P->sN = (float)(((N / 2) % 2 ? -1.0 : 1.0) / sqrt((double)N));
   const int inner = N - 2 * (r - 1);
-  P->nband = N * N - (inner > 0 ? inner * inner : 0);
+  P->nband = P->periodic ? 0 : N * N - (inner > 0 ? inner * inner : 0);
   P->gram_nkx = (P->P1 + 15) / 16;
   cudaGetDevice(&P->dev);
 

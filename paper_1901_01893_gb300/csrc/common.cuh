@@ -83,10 +83,12 @@ struct DevReport {
 #define SMSM_PART_MAX 8192  // capacity of each partial-sum array (doubles)
 
 struct smsm_plan_s {
-  int L, Ns, Nc, N, r, C, Cp /* C rounded up to even */, M, Ldiv, P1 /* N-r+1 */, R2 /* 2r-1 */;
+  int L, Ns, Nc, N, r, C, Cp /* C rounded up to even */, M, Ldiv, P1 /* origins per axis: N-r+1, or N if periodic */,
+      R2 /* 2r-1 */;
   int D;   // batch: independent problems (diffusion directions) sharing geometry and coil maps
   int flags;      // smsm_opts.flags
   int precision;  // smsm_opts.precision
+  int periodic;   // smsm_opts.boundary == PERIODIC: patch origins over all of [0, N)^2, mod N
   int gram_tc;    // 1: tensor-core Gram
   int gram_tc_nG; // split-K partials of the tensor-core Gram
   float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials

@@ -58,17 +58,19 @@ __device__ __forceinline__ bool gtc_wait(uint64_t* mbar, uint32_t parity, volati
 // shared-memory layout of one CTA (bytes); the same function sizes the launch
 struct GtcLayout {
   int rows_alloc;    // 128 * number of row tiles
-  int wp;            // window row pitch (complex elements): N + 8, shifts consecutive rows by 8 banks
+  int wp;            // window row pitch (complex elements): N + 8 (+16), shifts consecutive rows by 8 banks
+  int ext;           // periodic: the first ext (even, >= r-1) elements of a row repeated after it
   size_t arr_bytes;  // one of hi / lo of one staged chunk: rows_alloc x (32 GTC_KSTEP) bytes
   size_t win_elems;  // one window: Ns*r rows of wp elements
   int nst;           // ring stages (3, or 2 when three do not fit)
   size_t total;
 };
 
-__host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp) {
+__host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp, int periodic) {
   GtcLayout L;
   L.rows_alloc = 128 * ((2 * Cp + 127) / 128);
-  L.wp = N + 8;
+  L.ext = periodic ? ((r - 1 + 1) & ~1) : 0;
+  L.wp = N + (L.ext > 8 ? 24 : 8);
   L.arr_bytes = (size_t)L.rows_alloc * 32 * GTC_KSTEP;
   L.win_elems = (size_t)Ns * r * L.wp;
   const size_t win = 2 * L.win_elems * 8;
@@ -84,7 +86,7 @@ __host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp) {
 template <int PREC>
 __global__ void __launch_bounds__(GTC_THREADS, 1)
     k_gram_tc(const float2* __restrict__ x, float* __restrict__ Rpart, int* __restrict__ errflag, int Ns, int N,
-              int r, int C, int Cp, int nG) {
+              int r, int C, int Cp, int nG, int P1, int periodic) {
   constexpr int ESZ = PREC == 0 ? 4 : 2;         // bytes per operand element
   constexpr int EPC = 16 / ESZ;                  // elements per 16-byte core-matrix row
   constexpr int KQ = 2 * GTC_KSTEP;              // core matrices along K per chunk
@@ -100,12 +102,11 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const int t = blockIdx.x, g = blockIdx.y, lf = blockIdx.z;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R2C = 2 * Cp;
-  const GtcLayout Lo = gtc_layout(Ns, N, r, Cp);
+  const GtcLayout Lo = gtc_layout(Ns, N, r, Cp, periodic);
   const int NST = Lo.nst;
   const size_t arr_bytes = Lo.arr_bytes;
   const int WP = Lo.wp;
   float2* win = reinterpret_cast<float2*>(gsm + 2 * NST * arr_bytes);  // [2][Ns*r][WP]
-  const int P1 = N - r + 1;
   const int ky0 = (int)((long)g * P1 / nG), ky1 = (int)((long)(g + 1) * P1 / nG);
   const int nchx = (P1 + KCH - 1) / KCH;
   const int nit = (ky1 - ky0) * nchx;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const float2* xl = x + (size_t)lf * Ns * NN;
   const bool need_h0 = Cp > 128 * t;  // columns [0, Cp) reach the upper triangle of this row tile
   const int c_begin = need_h0 ? 0 : Cp;
-  const uint32_t win_bytes = (uint32_t)((size_t)Ns * r * N * sizeof(float2));
+  const uint32_t win_bytes = (uint32_t)((size_t)Ns * r * (N + Lo.ext) * sizeof(float2));
   const int tmem_cols = R2C > 256 ? 512 : 256;
 
   for (size_t e = tid; e < 2 * NST * arr_bytes / 16; e += GTC_THREADS)
@@ -140,13 +141,18 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const uint32_t tmem = tmem_base;
 
   // window ky -> buffer b: image rows ky..ky+r-1 of every shot, one TMA bulk copy per row
+  // (periodic: rows mod N, and the row's first ext elements copied again after it)
   auto load_window = [&](int ky, int b) {
     fence_async_smem();
     mbar_arrive_expect_tx(&win_b[b], win_bytes);
     for (int ip = 0; ip < Ns * r; ++ip) {
       const int i = ip / r, py = ip - i * r;
-      tma_bulk_g2s(win + (size_t)b * Lo.win_elems + (size_t)ip * WP, xl + (size_t)i * NN + (size_t)(ky + py) * N,
-                   (uint32_t)(N * sizeof(float2)), &win_b[b]);
+      int row = ky + py;
+      if (row >= N) row -= N;
+      float2* dst = win + (size_t)b * Lo.win_elems + (size_t)ip * WP;
+      const float2* src = xl + (size_t)i * NN + (size_t)row * N;
+      tma_bulk_g2s(dst, src, (uint32_t)(N * sizeof(float2)), &win_b[b]);
+      if (Lo.ext) tma_bulk_g2s(dst + N, src, (uint32_t)(Lo.ext * sizeof(float2)), &win_b[b]);
     }
   };
 
@@ -355,13 +361,13 @@ __global__ void k_gram_tc_reduce(const float* __restrict__ Rpart, double2* __res
   }
 }
 
-static size_t gram_tc_smem_for(int C, int Ns, int r, int N) {
-  return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16)).total;
+static size_t gram_tc_smem_for(int C, int Ns, int r, int N, int periodic) {
+  return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16), periodic).total;
 }
 
 // 2Cp <= 288 TMEM columns; the ring and two patch-row windows in shared memory
 int gram_tc_supported(const smsm_plan_s* P) {
-  return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N) <= 224 * 1024;
+  return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic) <= 224 * 1024;
 }
 
 int gram_tc_cp(const smsm_plan_s* P) { return 16 * ((P->C + 15) / 16); }
@@ -382,7 +388,9 @@ int gram_tc_nG(const smsm_plan_s* P) {
   return nG;
 }
 
-static size_t gram_tc_smem(const smsm_plan_s* P) { return gram_tc_smem_for(P->C, P->Ns, P->r, P->N); }
+static size_t gram_tc_smem(const smsm_plan_s* P) {
+  return gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic);
+}
 
 smsm_status gram_tc_init_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
@@ -402,10 +410,10 @@ smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cu
   dim3 grid(ntile, nG, P->LD);
   if (P->precision == SMSM_PRECISION_BF16_SPLIT)
     k_gram_tc<1><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
-                                                                 nG);
+                                                                 nG, P->P1, P->periodic);
   else
     k_gram_tc<0><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
-                                                                 nG);
+                                                                 nG, P->P1, P->periodic);
   SMSM_LAUNCH_CHECK("k_gram_tc");
   k_gram_tc_reduce<<<512, 256, 0, s>>>(P->Rpart, G, P->LD, P->C, Cp, nG);
   SMSM_LAUNCH_CHECK("k_gram_tc_reduce");

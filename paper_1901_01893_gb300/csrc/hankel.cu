@@ -22,7 +22,7 @@
 #define GCH 16  // patch-origin chunk edge
 
 __global__ void __launch_bounds__(256) k_gram_part(const float2* __restrict__ x, double2* __restrict__ part, int Ns,
-                                                   int N, int r, int C, int P1, int nkx, int tside) {
+                                                   int N, int r, int C, int P1, int nkx, int tside, int periodic) {
   extern __shared__ float2 xs[];
   const int TW = GCH + r - 1;  // window edge
   const int l = blockIdx.z;
@@ -63,6 +63,10 @@ __global__ void __launch_bounds__(256) k_gram_part(const float2* __restrict__ x,
       int i = e / (TW * TW), rem = e - i * TW * TW;
       int yy = rem / TW, xx = rem - yy * TW;
       int gy = ky0 + yy, gx = kx0 + xx;
+      if (periodic) {  // origins over all of [0, N)^2, indices mod N
+        gy %= N;
+        gx %= N;
+      }
       xs[e] = (gy < N && gx < N) ? xl[((size_t)i * N + gy) * N + gx] : cmk(0.f, 0.f);
     }
     __syncthreads();
@@ -135,7 +139,7 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
   const int TW = GCH + P->r - 1;
   size_t sm = (size_t)P->Ns * TW * TW * sizeof(float2);
   dim3 grid(nkx, ntile, P->LD);
-  k_gram_part<<<grid, 256, sm, s>>>(x, P->Gpart, P->Ns, P->N, P->r, P->C, P->P1, nkx, tside);
+  k_gram_part<<<grid, 256, sm, s>>>(x, P->Gpart, P->Ns, P->N, P->r, P->C, P->P1, nkx, tside, P->periodic);
   SMSM_LAUNCH_CHECK("k_gram_part");
   k_gram_reduce<<<256, 256, 0, s>>>(P->Gpart, G, P->LD, P->C, nkx);
   SMSM_LAUNCH_CHECK("k_gram_reduce");
@@ -169,7 +173,7 @@ __device__ __forceinline__ float2 filt_a(const float2* wi, int ldw, int r, int d
 }
 
 __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, float2* __restrict__ dcls,
-                                                 float2* __restrict__ wper, int Ns, int r, int C) {
+                                                 float2* __restrict__ wper, int Ns, int r, int C, int classes) {
   extern __shared__ float2 sW[];  // [r*r (q)][C + 1]
   const int R2 = 2 * r - 1, RR = R2 * R2;
   const int j = blockIdx.x;
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, f
     for (int py = 0; py < r; ++py)
       for (int px = 0; px < r; ++px) sp = cadd(sp, filt_a(wi, ldw, r, dy, dx, py, px));
     wper[((size_t)(l * Ns + i) * Ns + j) * RR + d] = sp;
+    if (!classes) continue;  // periodic patches: no border band, no class taps
     float2* out = dcls + ((size_t)l * RR * Ns + j) * RR * Ns + (size_t)d * Ns + i;  // + cls * Ns * RR * Ns
     const size_t cstride = (size_t)Ns * RR * Ns;
     // pass 0: rows 0..cy (classes cy <= r-1); pass 1: rows cy-r+1..r-1 (classes cy >= r-1)
@@ -276,8 +281,8 @@ smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2*
 }
 
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s) {
-  k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, P->wcls, P->wper, P->Ns, P->r,
-                                                              P->C);  // wcls holds the class taps dcls
+  k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C,
+                                                              !P->periodic);  // wcls holds the class taps dcls
   SMSM_LAUNCH_CHECK("k_filters");
   dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->LD);
   k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
@@ -509,7 +514,7 @@ static int band_chunks(const smsm_plan_s* P) {
 
 // partial sums per direction written by k_band and k_band_corner
 int band_blocks(const smsm_plan_s* P) {
-  return P->r > 1 ? P->L * 4 * band_chunks(P) + P->L * 4 * (P->r - 1) * (P->r - 1) : 0;
+  return (P->r > 1 && !P->periodic) ? P->L * 4 * band_chunks(P) + P->L * 4 * (P->r - 1) * (P->r - 1) : 0;
 }
 
 static size_t band_smem(const smsm_plan_s* P) {
@@ -548,7 +553,7 @@ smsm_status band_init_attrs(const smsm_plan_s* P) {
 
 smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, float scale, double* dot_part,
                         cudaStream_t s) {
-  if (P->r <= 1) {  // filter 1: every patch is valid, the periodic value is exact
+  if (P->r <= 1 || P->periodic) {  // filter 1 or periodic patches: the periodic value is exact
     if (dot_part) SMSM_CUDA_TRY(cudaMemsetAsync(dot_part, 0, sizeof(double) * SMSM_PART_MAX * P->D, s));
     return SMSM_OK;
   }

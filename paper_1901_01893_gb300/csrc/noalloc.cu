@@ -37,7 +37,7 @@ static __device__ __align__(256) double2 g_gram_scratch[SMSM_NOALLOC_SCRATCH_BYT
 
 // Gram kernels (hankel.cu)
 __global__ void k_gram_part(const float2* __restrict__ x, double2* __restrict__ part, int Ns, int N, int r, int C,
-                            int P1, int nkx, int tside);
+                            int P1, int nkx, int tside, int periodic);
 __global__ void k_gram_reduce(const double2* __restrict__ part, double2* __restrict__ G, int L, int C, int nkx);
 
 static std::mutex g_scratch_mu;
@@ -104,7 +104,7 @@ extern "C" smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, 
   for (int l = 0; l < mb; ++l) {
     const float2* xl = (const float2*)x + (size_t)l * shots * NN;
     double2* Gl = (double2*)G + (size_t)l * C * C;
-    k_gram_part<<<dim3(nkx, ntile, 1), 256, sm, s>>>(xl, scratch, shots, N, r, C, P1, nkx, tside);
+    k_gram_part<<<dim3(nkx, ntile, 1), 256, sm, s>>>(xl, scratch, shots, N, r, C, P1, nkx, tside, 0);
     SMSM_LAUNCH_CHECK("k_gram_part (no-alloc)");
     k_gram_reduce<<<128, 256, 0, s>>>(scratch, Gl, 1, C, nkx);
     SMSM_LAUNCH_CHECK("k_gram_reduce (no-alloc)");

@@ -20,6 +20,8 @@ SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_FLAG_GENERIC_KERNELS = 1
 SMSM_FLAG_PER_COIL_NORMAL = 2
+SMSM_BOUNDARY_VALID = 0
+SMSM_BOUNDARY_PERIODIC = 1
 SMSM_PRECISION_FP32, SMSM_PRECISION_BF16_SPLIT = 0, 1
 SMSM_MAX_OUTER = 128
 STAGES = ["adjoint", "gram", "eig", "vapply", "weights", "filters", "rowfft_inv", "column", "rowfft_fwd",
@@ -29,7 +31,7 @@ STAGE = {name: k for k, name in enumerate(STAGES)}
 
 class Opts(ctypes.Structure):
     _fields_ = [("caipi_div", ctypes.c_int), ("batch", ctypes.c_int), ("flags", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Params(ctypes.Structure):
@@ -145,13 +147,13 @@ class Plan:
     """
 
     def __init__(self, mb: int, shots: int, coils: int, n: int, filter: int, caipi_div: int = 0,
-                 batch: int = 1, flags: int = 0, precision: int = 0):
+                 batch: int = 1, flags: int = 0, precision: int = 0, boundary: int = 0):
         self.L, self.Ns, self.Nc, self.N, self.r = mb, shots, coils, n, filter
         self.D = batch
         self.C = shots * filter * filter
         self.M = n // shots if shots else 0
         h = ctypes.c_void_p()
-        opts = Opts(caipi_div=caipi_div, batch=batch, flags=flags, precision=precision)
+        opts = Opts(caipi_div=caipi_div, batch=batch, flags=flags, precision=precision, boundary=boundary)
         _check(lib().smsm_plan(ctypes.byref(h), mb, shots, coils, n, n, filter, ctypes.byref(opts)))
         self._h = h
 

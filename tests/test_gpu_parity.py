@@ -281,6 +281,35 @@ def test_batch_matches_single_problems(smsm):
     assert O.nrmse(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
 
 
+def test_periodic_boundary_parity(smsm):
+    # PERIODIC patches (every origin, indices mod N): Gram on both Gram paths, the
+    # penalty (multiplier only, no border band) and a short solve against the oracle.
+    key = "tiny"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    C = Ns * r * r
+    rng = np.random.default_rng(41)
+    x = crandn(rng, L, Ns, N, N)
+    x32 = x.astype(np.complex64).astype(complex)
+    W = _random_weight(rng, L, C)
+    W32 = W.astype(np.complex64).astype(complex)
+    Gref = O.gram(x32, r, periodic=True)
+    for flags in (0, smsm.SMSM_FLAG_GENERIC_KERNELS):
+        p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, flags=flags, boundary=smsm.SMSM_BOUNDARY_PERIODIC)
+        assert O.nrmse(p.hankel_gram(c64(x)).cpu().numpy(), Gref) < OP_TOL
+        pen = p.apply_filters(c128(W), c64(x)).cpu().numpy()
+        assert O.nrmse(pen, O.penalty(x32, W32, r, periodic=True)) < OP_TOL
+    g, xt, y = _problem(key, 7)
+    p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, boundary=smsm.SMSM_BOUNDARY_PERIODIC)
+    p.set_sens(c64(g["sens"]))
+    prm = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4)
+    xo, rep = p.reconstruct(c64(y), params=prm)
+    assert rep.status == 0
+    ref = O.reconstruct(y, g["sens"], r, dict(K=3, J=4, lam=1e-2, periodic=True), Ldiv=Ldiv)
+    err = O.nrmse(xo.cpu().numpy(), ref)
+    print(f"periodic: reconstruct NRMSE vs oracle {err:.3e}")
+    assert err < SOLVE_TOL
+
+
 def test_lanes_give_identical_results(smsm):
     # Solving the batch as 1, 2 or 3 concurrent lanes (sub-batches on their own
     # graph branches) changes the schedule only: every direction runs the same
