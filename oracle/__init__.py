@@ -20,11 +20,14 @@ Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
                               periodic boundary: W = I and FFT agreement
                               at every pixel)
 * cg ........................ pinned (exact solve in n steps, small SPD)
+* sense ..................... pinned (least squares by a dense normal-equation
+                              solve at N = 8; exact recovery of a phase-free
+                              object)
 * reconstruct ............... pinned (exact recovery with full sampling;
                               slice-phase equivariance; noiseless recovery)
 """
 from .smsm_oracle import *  # noqa: F401,F403
 from .smsm_oracle import (DEFAULT_PARAMS, adjoint, caipi_ramp, cg, fft2c, forward, gram,  # noqa: F401
-                          hankel, hankel_adjoint, ifft2c, irls_weight, magnitude, make_data,
+                          hankel, hankel_adjoint, ifft2c, sense, irls_weight, magnitude, make_data,
                           normal, nrmse, nullspace_weight, penalty, reconstruct, shot_lines,
                           vdot)

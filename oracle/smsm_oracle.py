@@ -302,6 +302,24 @@ def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = N
     return x
 
 
+def sense(y: np.ndarray, sens: np.ndarray, L: int, J: int, phase: np.ndarray | None = None,
+          Ldiv: int | None = None) -> np.ndarray:
+    """SMS-SENSE, the comparison reconstruction of the paper's figures: the k-space
+    data of all shots combined into one k-space per slice (the shot-shared model of
+    Eq. 4, with the image-domain phase ``phase`` or, when it is None, without any
+    phase correction) and the slices unfolded by least squares, J CG steps on
+    A^H A x = A^H y from x = 0.  Returns x [L][1][N][N]."""
+    Ns, _, _, N = y.shape
+    ph = np.ones((L, Ns, N, N), dtype=np.complex128) if phase is None else phase
+    b = adjoint(y, sens, L, Ldiv=Ldiv, phase=ph)
+
+    def apply_N(v):
+        return adjoint(forward(v, sens, Ldiv=Ldiv, phase=ph), sens, L, Ldiv=Ldiv, phase=ph)
+
+    x, _ = cg(apply_N, b, np.zeros_like(b), J)
+    return x
+
+
 # ---------------------------------------------------------------------------
 # Outputs and error measures
 # ---------------------------------------------------------------------------

@@ -327,6 +327,30 @@ def test_periodic_penalty_identity_weight_and_fft_convolution():
     assert np.allclose(O.penalty(x, W, r, periodic=True), ref, atol=1e-10)
 
 
+# --- SMS-SENSE comparison reconstruction --------------------------------------
+
+def test_sense_is_the_least_squares_solution():
+    # Dense route: the matrix of the shot-shared forward model (columns = images of the
+    # unit vectors), solved by numpy's least squares; CG to convergence must agree.
+    L, Ns, Nc, N = 2, 2, 3, 8
+    sens = crandn(L, Nc, N, N)
+    phase = np.exp(1j * RNG.uniform(-np.pi, np.pi, (L, Ns, N, N)))
+    n = L * N * N
+    A = np.zeros((Ns * Nc * (N // Ns) * N, n), dtype=complex)
+    for k in range(n):
+        e = np.zeros(n, dtype=complex)
+        e[k] = 1.0
+        A[:, k] = O.forward(e.reshape(L, 1, N, N), sens, phase=phase).ravel()
+    y = crandn(Ns, Nc, N // Ns, N)
+    x_ls = np.linalg.lstsq(A, y.ravel(), rcond=None)[0].reshape(L, 1, N, N)
+    x_cg = O.sense(y, sens, L, J=3 * n, phase=phase)
+    assert O.nrmse(x_cg, x_ls) < 1e-8
+    # no phase given = unit phase (no phase correction)
+    x0 = O.sense(y, sens, L, J=40)
+    x1 = O.sense(y, sens, L, J=40, phase=np.ones((L, Ns, N, N), dtype=complex))
+    assert np.allclose(x0, x1, atol=1e-12)
+
+
 # --- CG ------------------------------------------------------------------------
 
 def test_cg_solves_small_hpd_system_exactly():
