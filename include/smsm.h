@@ -243,6 +243,18 @@ smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const sms
                              smsm_report* report, void* stream);
 
 /*
+ * SMS-SENSE, the comparison reconstruction of the paper's simulation and in-vivo
+ * figures (Results): the k-space data of all shots are combined into one k-space per
+ * slice (the shot-shared model of Eq. 4: phase phi_{l,i} [D][L][Ns][N][N] complex64,
+ * image domain, or phase == NULL for no phase correction) and the slices are unfolded
+ * by least squares: cg_iters steps of CG on A^H A x = A^H y from x = 0.
+ *   y: [D][Ns][Nc][N/Ns][N] complex64; x: [D][L][1][N][N] complex64 (overwritten).
+ * Runs on the stream without a graph; `report` (nullable) gets the status after a sync.
+ */
+smsm_status smsm_sense(smsm_plan_t plan, const void* y, const void* phase, void* x, int cg_iters,
+                       smsm_report* report, void* stream);
+
+/*
  * Centred unitary 2D DFT of `count` N x N complex64 images (Fig. 1 steps
  * (i)/(iii)): inverse != 0 selects F^-1.  in and out may alias.
  */

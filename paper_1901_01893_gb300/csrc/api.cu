@@ -529,3 +529,18 @@ extern "C" smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x
   }
   return solver_reconstruct(plan, y, x, &p, report, S(stream));
 }
+
+extern "C" smsm_status smsm_sense(smsm_plan_t plan, const void* y, const void* phase, void* x, int cg_iters,
+                                  smsm_report* report, void* stream) {
+  CHECK_PLAN("smsm_sense");
+  CHECK_PTR("smsm_sense", y);
+  CHECK_PTR("smsm_sense", x);
+  if (phase) CHECK_PTR("smsm_sense", phase);
+  smsm_status st;
+  if ((st = need_sens(plan, "smsm_sense"))) return st;
+  if (cg_iters < 0) {
+    smsm_set_error("smsm_sense: cg_iters must be >= 0");
+    return SMSM_ERR_ARG;
+  }
+  return solver_sense(plan, y, phase, x, cg_iters, report, S(stream));
+}

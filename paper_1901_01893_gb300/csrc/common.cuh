@@ -271,5 +271,7 @@ int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
                                smsm_report* report, cudaStream_t s);
 void solver_free_timing(smsm_plan_s* P);
+smsm_status solver_sense(smsm_plan_s* P, const void* y, const void* phase, void* x, int J, smsm_report* report,
+                         cudaStream_t s);
 smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
                              cudaStream_t s);

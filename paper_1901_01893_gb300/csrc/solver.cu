@@ -162,6 +162,26 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_pupdate(const float4* __rest
   }
 }
 
+// partials of Re<a, b> (FP32 per thread, FP64 per CTA), [D][SMSM_PART_MAX]
+__global__ void __launch_bounds__(VEC_THREADS) k_vdot_part(const float4* __restrict__ a, const float4* __restrict__ b,
+                                                           size_t n4, double* __restrict__ part) {
+  __shared__ double red[VEC_THREADS];
+  DIR_OFFSETS(n4)
+  a += off_;
+  b += off_;
+  float s = 0.f;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    const float4 u = a[e], v = b[e];
+    s = fmaf(u.x, v.x, fmaf(u.y, v.y, fmaf(u.z, v.z, fmaf(u.w, v.w, s))));
+  }
+  block_partial((double)s, red, part + poff_);
+}
+
+__global__ void k_fill_one(float2* __restrict__ v, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    v[e] = cmk(1.f, 0.f);
+}
+
 // which = 0: record ||r||^2 of direction 0 at the start of outer iteration `outer`; 1: at its end
 __global__ void k_record(DevReport* rep, int outer, int which, const double* __restrict__ rr, int nrr) {
   __shared__ double red[VEC_THREADS];
@@ -466,6 +486,70 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
         report->stage_launches[tp->stage[k]] += 1;
       }
     }
+  }
+  return SMSM_OK;
+}
+
+// SMS-SENSE (the comparison reconstruction of the paper's figures): one k-space per
+// slice shared by the shots (Eq. 4 with the given image-domain phase, or unit phase:
+// no phase correction), slices unfolded by least squares -- J CG steps on
+// A^H A x = A^H y from x = 0.  A^H A is the forward column stage followed by the
+// adjoint one (the data-side x transforms of A and A^H cancel, so they are skipped).
+smsm_status solver_sense(smsm_plan_s* P, const void* y, const void* phase, void* x, int J, smsm_report* report,
+                         cudaStream_t s) {
+  smsm_status st;
+  const int L = P->L, Ns = P->Ns, N = P->N, D = P->D;
+  const size_t NN = (size_t)N * N;
+  const size_t nx = (size_t)D * L * NN;  // shared k-space per slice
+  const size_t ny = (size_t)D * Ns * P->Nc * P->M * N;
+  const size_t n4 = (size_t)L * NN / 2;
+  const int nvb = vec_blocks(P);
+  const dim3 vg(nvb, D);
+  double* rr0 = P->part_rr;
+  double* rr1 = P->part_rr + (size_t)SMSM_PART_MAX * D;
+  SMSM_CUDA_TRY(cudaMemcpyAsync(P->ybuf, y, sizeof(float2) * ny, cudaMemcpyDeviceToDevice, s));
+  if (phase) {
+    if ((st = launch_transpose((const float2*)phase, P->phaseT, D * L * Ns, N, N, s))) return st;
+  } else {
+    k_fill_one<<<256, 256, 0, s>>>(P->phaseT, (size_t)D * L * Ns * NN);
+    SMSM_LAUNCH_CHECK("k_fill_one");
+  }
+  k_reset_state<<<1, 128, 0, s>>>(P->st, D);
+  SMSM_LAUNCH_CHECK("k_reset_state");
+  // b = A^H y
+  if ((st = launch_rowfft_out_T(P, P->ybuf, P->yh, D * Ns * P->Nc, P->M, 1, s))) return st;
+  if ((st = launch_col(P, COL_ADJ, 1, P->yh, P->hB, P->phaseT, nullptr, 0.f, nullptr, s))) return st;
+  if ((st = launch_rowfft_in_T(P, P->hB, P->bv, D * L, N, 0, s))) return st;
+  SMSM_CUDA_TRY(cudaMemsetAsync(P->xs, 0, sizeof(float2) * nx, s));
+  SMSM_CUDA_TRY(cudaMemsetAsync(P->qv, 0, sizeof(float2) * nx, s));
+  k_cg_init<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->bv, (const float4*)P->qv, (float4*)P->rv, (float4*)P->pv,
+                                        n4, rr0);
+  SMSM_LAUNCH_CHECK("k_cg_init");
+  for (int j = 0; j < J; ++j) {
+    double* rin = (j & 1) ? rr1 : rr0;
+    double* rout = (j & 1) ? rr0 : rr1;
+    if ((st = launch_rowfft_out_T(P, P->pv, P->hA, D * L, N, 1, s))) return st;
+    if ((st = launch_col(P, COL_FWD, 1, P->hA, P->yh, P->phaseT, nullptr, 0.f, nullptr, s))) return st;
+    if ((st = launch_col(P, COL_ADJ, 1, P->yh, P->hB, P->phaseT, nullptr, 0.f, nullptr, s))) return st;
+    if ((st = launch_rowfft_in_T(P, P->hB, P->qv, D * L, N, 0, s))) return st;
+    k_vdot_part<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->pv, (const float4*)P->qv, n4, P->part_pq_col);
+    SMSM_LAUNCH_CHECK("k_vdot_part");
+    k_cg_update<<<vg, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
+                                            (const float4*)P->qv, n4, P->part_pq_col, nvb, P->part_pq_band, 0, rin,
+                                            nvb, rout, P->st);
+    SMSM_LAUNCH_CHECK("k_cg_update");
+    k_cg_pupdate<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
+    SMSM_LAUNCH_CHECK("k_cg_pupdate");
+  }
+  SMSM_CUDA_TRY(cudaMemcpyAsync(x, P->xs, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
+  if (report) {
+    std::vector<SolverState> hs(P->D);
+    SMSM_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->st, sizeof(SolverState) * P->D, cudaMemcpyDeviceToHost, s));
+    SMSM_CUDA_TRY(cudaStreamSynchronize(s));
+    memset(report, 0, sizeof(*report));
+    for (int d = 0; d < P->D && !report->status; ++d) report->status = hs[d].status;
+    report->lanes = 1;
+    report->lane0_batch = P->D;
   }
   return SMSM_OK;
 }

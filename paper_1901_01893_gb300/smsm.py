@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
     L.smsm_reconstruct.restype = st
     L.smsm_fft2c.argtypes = [vp, vp, vp, i, i, vp]
     L.smsm_fft2c.restype = st
+    L.smsm_sense.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(Report), vp]
+    L.smsm_sense.restype = st
     L.smsm_hankel_gram_noalloc.argtypes = [vp, vp, i, i, i, i, vp]
     L.smsm_hankel_gram_noalloc.restype = st
     L.smsm_plan_device_status.argtypes = [vp, vp]
@@ -250,6 +252,20 @@ class Plan:
         return x, rep
 
     reconstruct = smsm_reconstruct
+
+    def smsm_sense(self, y: torch.Tensor, phase: torch.Tensor | None = None, cg_iters: int = 30,
+                   x: torch.Tensor | None = None, report: bool = True):
+        """SMS-SENSE comparison reconstruction: returns (x [.., L, 1, N, N], Report or None)."""
+        xs = self._b((self.L, 1, self.N, self.N))
+        if x is None:
+            x = torch.empty(xs, dtype=torch.complex64, device=y.device)
+        pp = _dev(phase, self.x_shape, "phase") if phase is not None else None
+        rep = Report() if report else None
+        _check(lib().smsm_sense(self._h, _dev(y, self.y_shape, "y"), pp, _dev(x, xs, "x"), int(cg_iters),
+                                ctypes.byref(rep) if rep is not None else None, _stream()))
+        return x, rep
+
+    sense = smsm_sense
 
     def smsm_fft2c(self, t: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None):
         if out is None:

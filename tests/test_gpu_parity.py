@@ -310,6 +310,28 @@ def test_periodic_boundary_parity(smsm):
     assert err < SOLVE_TOL
 
 
+@pytest.mark.parametrize("with_phase", [False, True])
+def test_sms_sense_parity(smsm, with_phase):
+    # SMS-SENSE (shots combined, one k-space per slice, least squares by CG) with and
+    # without the shot phase, against the oracle's same J steps; batch of 2.
+    key = "tiny"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    D, J = 2, 12
+    g, xt, y0 = _problem(key, 9)
+    rng = np.random.default_rng(51)
+    ys = np.stack([y0, y0 * np.exp(0.4j) + 0.05 * crandn(rng, *y0.shape)])
+    ph = np.stack([g["phase"], np.conj(g["phase"])]) if with_phase else None
+    p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    p.set_sens(c64(g["sens"]))
+    x, rep = p.sense(c64(ys), phase=c64(ph) if with_phase else None, cg_iters=J)
+    assert rep.status == 0
+    x = x.cpu().numpy()
+    for d in range(D):
+        ref = O.sense(ys[d], g["sens"], L, J, phase=ph[d] if with_phase else None, Ldiv=Ldiv)
+        err = O.nrmse(x[d], ref)
+        assert err < 1e-4, err
+
+
 def test_lanes_give_identical_results(smsm):
     # Solving the batch as 1, 2 or 3 concurrent lanes (sub-batches on their own
     # graph branches) changes the schedule only: every direction runs the same
