@@ -52,6 +52,8 @@ __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z ==
 // triangle is an (n/2) x (n+1) rectangle of block indices.
 // warm != 0: start from Gw = V_prev^H G V_prev (symmetrised on load).
 
+#define JAC_BLK 4  // blocks per thread: (Cp/2 rounded to even)/2 * (that + 1) <= 4 * 1024 for Cp <= 180
+
 // block bi of the folded triangle -> (k1, k2), k1 <= k2 < n (n even)
 __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, int& k2) {
   int fr = __float2int_rz(((float)bi + 0.5f) * inv_n1);
@@ -109,6 +111,17 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   __syncthreads();
   // rotations below this absolute size only churn rounding noise
   const float floor_abs = 1e-7f * dmax;
+  // this thread's blocks of the folded triangle, the same in every round
+  int kb1[JAC_BLK], kb2[JAC_BLK];
+#pragma unroll
+  for (int m = 0; m < JAC_BLK; ++m) {
+    const int bi = tid + m * nt;
+    kb1[m] = kb2[m] = -1;
+    if (bi < nblk) {
+      tri_block(bi, nh, inv_n1, kb1[m], kb2[m]);
+      if (kb2[m] >= half) kb1[m] = -1;  // virtual pair of an odd half
+    }
+  }
   int sw = 0;
   for (; sw < max_sweeps; ++sw) {
     int rotated = 0;  // this thread set a non-identity rotation during the sweep
@@ -133,10 +146,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
         rlog[(((size_t)l * SMSM_MAX_SWEEPS + sw) * (Cp - 1) + round) * half + tid] = J;
       }
       __syncthreads();
-      for (int bi = tid; bi < nblk; bi += nt) {
-        int k1, k2;
-        tri_block(bi, nh, inv_n1, k1, k2);
-        if (k2 >= half) continue;  // virtual pair of an odd half
+#pragma unroll
+      for (int m = 0; m < JAC_BLK; ++m) {
+        const int k1 = kb1[m], k2 = kb2[m];
+        if (k1 < 0) continue;
         const float4 J1 = rot[k1];
         const bool id1 = is_ident(J1);
         const int p1 = rp[k1], q1 = rq[k1];
@@ -406,6 +419,11 @@ static size_t jacobi_smem(int Cp) {
 }
 
 smsm_status eig_init_attrs(int Cp) {
+  const int nh = (Cp / 2 + 1) & ~1;
+  if ((nh / 2) * (nh + 1) > JAC_BLK * 1024) {
+    smsm_set_error("Jacobi kernel: C = %d is above its block schedule's limit", Cp);
+    return SMSM_ERR_ARG;
+  }
   size_t sm = jacobi_smem(Cp);
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
