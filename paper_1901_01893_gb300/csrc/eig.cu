@@ -203,19 +203,20 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
 }
 
 // V = V0 * (product of the logged rotations), V0 = I or the previous V (warm).
-// One CTA per (matrix, 8 VA_ROWS_PER_WARP rows); each warp owns VA_ROWS_PER_WARP
+// One CTA per (matrix, VA_WARPS VA_ROWS_PER_WARP rows); each warp owns VA_ROWS_PER_WARP
 // rows in shared memory and applies every round's rotations to them.  Lane j
 // handles the pairs k = j + 32 u; their indices advance by one (mod Cp-1) from
 // round to round, and the next round's rotations are loaded while the current
 // ones are applied.
-#define VA_ROWS_PER_WARP 8
-#define VA_SLOTS 6  // pair slots per lane: Cp/2 <= 32 VA_SLOTS
-__global__ void __launch_bounds__(256) k_vapply(const float4* __restrict__ rlog, const int* __restrict__ sweeps,
+#define VA_ROWS_PER_WARP 4
+#define VA_WARPS 12  // 48 rows per CTA: three CTAs cover the 144 rows of the common C = 144
+#define VA_SLOTS 3   // pair slots per lane: Cp/2 <= 32 VA_SLOTS (Cp <= 192)
+__global__ void __launch_bounds__(32 * VA_WARPS) k_vapply(const float4* __restrict__ rlog, const int* __restrict__ sweeps,
                                                 float2* __restrict__ V, int C, int Cp, int warm) {
   extern __shared__ float2 rows[];
   const int l = blockIdx.x;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t0 = (blockIdx.y * 8 + w) * VA_ROWS_PER_WARP;
+  const int t0 = (blockIdx.y * VA_WARPS + w) * VA_ROWS_PER_WARP;
   float2* myrows = rows + (size_t)w * VA_ROWS_PER_WARP * Cp;
   float2* Vl = V + (size_t)l * C * C;
 #pragma unroll
@@ -430,7 +431,7 @@ smsm_status eig_init_attrs(int Cp) {
     smsm_set_error("Jacobi kernel cannot get %zu bytes of shared memory: %s", sm, cudaGetErrorString(e));
     return SMSM_ERR_ARG;
   }
-  const size_t vsm = (size_t)8 * VA_ROWS_PER_WARP * Cp * sizeof(float2);
+  const size_t vsm = (size_t)VA_WARPS * VA_ROWS_PER_WARP * Cp * sizeof(float2);
   e = cudaFuncSetAttribute(k_vapply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
   if (e != cudaSuccess) {
     smsm_set_error("rotation replay kernel cannot get %zu bytes of shared memory: %s", vsm, cudaGetErrorString(e));
@@ -461,8 +462,8 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  dim3 gv(P->LD, (C + 8 * VA_ROWS_PER_WARP - 1) / (8 * VA_ROWS_PER_WARP));
-  k_vapply<<<gv, 256, (size_t)8 * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
+  dim3 gv(P->LD, (C + VA_WARPS * VA_ROWS_PER_WARP - 1) / (VA_WARPS * VA_ROWS_PER_WARP));
+  k_vapply<<<gv, 32 * VA_WARPS, (size_t)VA_WARPS * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
                                                                               warm);
   SMSM_LAUNCH_CHECK("k_vapply");
   if (T) T->end(SMSM_STAGE_VAPPLY);
