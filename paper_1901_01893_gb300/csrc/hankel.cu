@@ -301,7 +301,7 @@ smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s
 // taps once per CTA; the corner pixels each have their own class and are
 // summed by k_band_corner.
 // ---------------------------------------------------------------------------
-#define BAND_P 4                  // pixels per thread
+#define BAND_P 2                  // pixels per thread
 #define BAND_TX (32 * BAND_P)     // pixels per strip line per CTA
 
 // One CTA = one chunk of BAND_TX pixels of one line of one strip; warp j sums
