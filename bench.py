@@ -202,6 +202,19 @@ class Clocks:
 # our arm
 # ---------------------------------------------------------------------------
 
+# DRAM bytes (read + write) per direction of one launch of each kernel class, from the
+# ncu captures summarised in profiles/ (plain workload, 26-direction launches divided by
+# 26; the traffic of these kernels grows in proportion to the directions a launch covers).
+# Only valid for the kernels as captured: a class whose kernel changes is dropped here.
+TRAFFIC_PER_DIRECTION = {
+    "eig": (8.663552e6 + 2.078208e6) / 26,      # profiles/k_jacobi_plain_128.md
+    "gram": (27.380480e6 + 10.442496e6) / 26,   # profiles/k_gram_tc_plain_128.md
+    "band": (34.552832e6 + 0.116480e6) / 26,    # profiles/k_band_plain_128.md
+    "column": (138.540544e6 + 12.339456e6) / 26,  # profiles/k_col_alias_plain_128.md
+    "vapply": (38.639616e6 + 0.875264e6) / 26,  # profiles/k_vapply_plain_128.md
+}
+
+
 def stage_work(cfg, D, sweeps):
     """Algorithmic work of one launch (bracket) of each kernel class, over a batch of D problems.
 
@@ -347,6 +360,8 @@ def run_ours(args):
     # timed brackets cover the launches of lane 0, each over its sub-batch of directions
     d_launch = rep.lane0_batch if rep.lanes > 1 else D
     bound, amount = stage_work(cfg, d_launch, sweeps)[dominant]
+    tpd = TRAFFIC_PER_DIRECTION.get(dominant) if WORKLOAD == "plain" else None
+    traffic = tpd * d_launch if tpd is not None else None
     per_launch_ms = dom_ms / max(dom_n, 1)
     sm_mhz = clocks.get("sm_mhz") or 1455.0
     if bound == "alu":
@@ -354,12 +369,12 @@ def run_ours(args):
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = amount / (per_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms,
+                "traffic": traffic, "kernel": dominant, "launch_ms": per_launch_ms,
                 "peak_note": f"FP32 FMA peak (152 SMs x 128 lanes x 2) at the sampled median SM clock {sm_mhz:.0f} MHz"}
     else:
         achieved = amount / (per_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "kernel": dominant, "launch_ms": per_launch_ms, "peak_note": peak_src}
+                "traffic": traffic, "kernel": dominant, "launch_ms": per_launch_ms, "peak_note": peak_src}
 
     # CPU baseline: the oracle as it stands, on a bounded sample of the same workload
     cpu = None
