@@ -64,7 +64,7 @@ static int pick_ty(int rows) {
 template <bool INV>
 __global__ void __launch_bounds__(256) k_rowfft_out_T(const float2* __restrict__ in, float2* __restrict__ out,
                                                       int rows, int TY, FftDesc d, const float2* __restrict__ tw,
-                                                      float sN) {
+                                                      float sN, int vec) {
   extern __shared__ float2 sm[];
   const int N = d.n, ld = N + 1;
   float2* b0 = sm;
@@ -73,16 +73,47 @@ __global__ void __launch_bounds__(256) k_rowfft_out_T(const float2* __restrict__
   const int b = blockIdx.y, r0 = blockIdx.x * TY;
   for (int e = threadIdx.x; e < N; e += blockDim.x) twS[e] = tw[e];
   const float2* src = in + ((size_t)b * rows + r0) * N;
-  for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
+  // the TY rows are contiguous: two complex values per 16-byte load, all of a thread's
+  // loads issued before any is used (N is even, so pairs never straddle a row)
+  const float4* src4 = reinterpret_cast<const float4*>(src);
+  const int n4 = vec ? TY * N / 2 : 0;
+  for (int e = threadIdx.x; !vec && e < TY * N; e += blockDim.x) {
     int row = e / N, col = e - row * N;
     b0[row * ld + col] = cscale(src[e], sgn_par(col));
+  }
+  for (int e0 = threadIdx.x; e0 < n4; e0 += 4 * blockDim.x) {
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k * blockDim.x;
+      if (e < n4) v[k] = __ldg(src4 + e);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k * blockDim.x;
+      if (e < n4) {
+        const int f = 2 * e, row = f / N, col = f - row * N;  // col even: signs +, -
+        b0[row * ld + col] = cmk(v[k].x, v[k].y);
+        b0[row * ld + col + 1] = cmk(-v[k].z, -v[k].w);
+      }
+    }
   }
   __syncthreads();
   float2* R = fft_smem<INV>(b0, b1, TY, ld, d, twS);
   float2* dst = out + (size_t)b * N * rows + r0;
-  for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
-    int col = e / TY, row = e - col * TY;
-    dst[(size_t)col * rows + row] = cscale(R[row * ld + col], sN * sgn_par(col));
+  if (vec && (TY & 1) == 0 && (rows & 1) == 0) {
+    // pairs of rows: 16-byte stores along each output line
+    for (int e = threadIdx.x; e < TY * N / 2; e += blockDim.x) {
+      const int col = e / (TY / 2), row = 2 * (e - col * (TY / 2));
+      const float sc = sN * sgn_par(col);
+      const float2 u = R[row * ld + col], w = R[(row + 1) * ld + col];
+      *reinterpret_cast<float4*>(dst + (size_t)col * rows + row) = make_float4(sc * u.x, sc * u.y, sc * w.x, sc * w.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
+      int col = e / TY, row = e - col * TY;
+      dst[(size_t)col * rows + row] = cscale(R[row * ld + col], sN * sgn_par(col));
+    }
   }
 }
 
@@ -90,7 +121,7 @@ __global__ void __launch_bounds__(256) k_rowfft_out_T(const float2* __restrict__
 template <bool INV>
 __global__ void __launch_bounds__(256) k_rowfft_in_T(const float2* __restrict__ in, float2* __restrict__ out,
                                                      int rows, int TY, FftDesc d, const float2* __restrict__ tw,
-                                                     float sN) {
+                                                     float sN, int vec) {
   extern __shared__ float2 sm[];
   const int N = d.n, ld = N + 1;
   float2* b0 = sm;
@@ -99,30 +130,71 @@ __global__ void __launch_bounds__(256) k_rowfft_in_T(const float2* __restrict__ 
   const int b = blockIdx.y, r0 = blockIdx.x * TY;
   for (int e = threadIdx.x; e < N; e += blockDim.x) twS[e] = tw[e];
   const float2* src = in + (size_t)b * N * rows + r0;
-  for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
-    int col = e / TY, row = e - col * TY;
-    b0[row * ld + col] = cscale(src[(size_t)col * rows + row], sgn_par(col));
+  if (vec && (TY & 1) == 0 && (rows & 1) == 0) {
+    // pairs of rows of each input line: 16-byte loads, a thread's loads issued together
+    const int n4 = TY * N / 2;
+    for (int e0 = threadIdx.x; e0 < n4; e0 += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + k * blockDim.x;
+        if (e < n4) {
+          const int col = e / (TY / 2), row = 2 * (e - col * (TY / 2));
+          v[k] = __ldg(reinterpret_cast<const float4*>(src + (size_t)col * rows + row));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + k * blockDim.x;
+        if (e < n4) {
+          const int col = e / (TY / 2), row = 2 * (e - col * (TY / 2));
+          const float sg = sgn_par(col);
+          b0[row * ld + col] = cmk(sg * v[k].x, sg * v[k].y);
+          b0[(row + 1) * ld + col] = cmk(sg * v[k].z, sg * v[k].w);
+        }
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
+      int col = e / TY, row = e - col * TY;
+      b0[row * ld + col] = cscale(src[(size_t)col * rows + row], sgn_par(col));
+    }
   }
   __syncthreads();
   float2* R = fft_smem<INV>(b0, b1, TY, ld, d, twS);
   float2* dst = out + ((size_t)b * rows + r0) * N;
-  for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
-    int row = e / N, col = e - row * N;
-    dst[e] = cscale(R[row * ld + col], sN * sgn_par(col));
+  if (vec) {
+    float4* dst4 = reinterpret_cast<float4*>(dst);
+    for (int e = threadIdx.x; e < TY * N / 2; e += blockDim.x) {
+      const int f = 2 * e, row = f / N, col = f - row * N;  // col even: signs +, -
+      const float2 u = R[row * ld + col], w = R[row * ld + col + 1];
+      dst4[e] = make_float4(sN * u.x, sN * u.y, -sN * w.x, -sN * w.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
+      int row = e / N, col = e - row * N;
+      dst[e] = cscale(R[row * ld + col], sN * sgn_par(col));
+    }
   }
 }
 
 static size_t rowfft_smem(int N, int TY) { return (size_t)(2 * TY * (N + 1) + N) * sizeof(float2); }
 
+// 16-byte vector accesses when both buffers allow them (callers' buffers may be offset)
+static int rowfft_vec(const void* in, const void* out) {
+  return !(((uintptr_t)in | (uintptr_t)out) & 15u);
+}
+
 smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
                                 int inverse, cudaStream_t s) {
   const int TY = pick_ty(rows);
+  const int vec = rowfft_vec(in, out);
   dim3 grid(rows / TY, nb);
   size_t sm = rowfft_smem(P->N, TY);
   if (inverse)
-    k_rowfft_out_T<true><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN);
+    k_rowfft_out_T<true><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN, vec);
   else
-    k_rowfft_out_T<false><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN);
+    k_rowfft_out_T<false><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN, vec);
   SMSM_LAUNCH_CHECK("k_rowfft_out_T");
   return SMSM_OK;
 }
@@ -130,12 +202,13 @@ smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* 
 smsm_status launch_rowfft_in_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
                                int inverse, cudaStream_t s) {
   const int TY = pick_ty(rows);
+  const int vec = rowfft_vec(in, out);
   dim3 grid(rows / TY, nb);
   size_t sm = rowfft_smem(P->N, TY);
   if (inverse)
-    k_rowfft_in_T<true><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN);
+    k_rowfft_in_T<true><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN, vec);
   else
-    k_rowfft_in_T<false><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN);
+    k_rowfft_in_T<false><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN, vec);
   SMSM_LAUNCH_CHECK("k_rowfft_in_T");
   return SMSM_OK;
 }
