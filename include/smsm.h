@@ -243,6 +243,18 @@ smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const sms
                              smsm_report* report, void* stream);
 
 /*
+ * Independent slice groups that may differ in geometry (MB, shots, coils, N,
+ * filter; one plan each, coil maps set) reconstructed together: every plan's
+ * captured solve (as smsm_reconstruct, same params for all) runs on that plan's
+ * own stream, forked from `stream` and joined back into it, so the kernels of
+ * small and large groups share the GPU.  ys[k], xs[k] are laid out as for
+ * smsm_reconstruct on plans[k]; a plan may appear only once.  `reports`
+ * (nullable) is an array of n, filled after a synchronisation of `stream`.
+ */
+smsm_status smsm_reconstruct_groups(int n, smsm_plan_t const* plans, const void* const* ys, void* const* xs,
+                                    const smsm_params* params, smsm_report* reports, void* stream);
+
+/*
  * SMS-SENSE, the comparison reconstruction of the paper's simulation and in-vivo
  * figures (Results): the k-space data of all shots are combined into one k-space per
  * slice (the shot-shared model of Eq. 4: phase phi_{l,i} [D][L][Ns][N][N] complex64,

@@ -506,6 +506,25 @@ extern "C" smsm_status smsm_plan_device_status(smsm_plan_t plan, void* stream) {
   return SMSM_OK;
 }
 
+// parameters of a solve on `plan`: defaults for NULL, then the range checks
+static smsm_status solve_params(smsm_plan_t plan, const smsm_params* params, smsm_params* p, const char* fn) {
+  if (params)
+    *p = *params;
+  else
+    smsm_default_params(p);
+  if (p->outer_iters < 0 || p->outer_iters > SMSM_MAX_OUTER || p->cg_iters < 0 || p->eta < 1.0 ||
+      !(p->lambda >= 0.0) || !(p->eps0_rel > 0.0) || !(p->eps_min_rel > 0.0) ||
+      (p->mode != SMSM_MODE_IRLS && p->mode != SMSM_MODE_NULLSPACE) ||
+      (p->mode == SMSM_MODE_NULLSPACE && (p->rank <= 0 || p->rank >= plan->C)) || p->lanes < 0 ||
+      p->lanes > SMSM_MAX_LANES) {
+    smsm_set_error("%s: invalid parameters (K in [0,%d], J >= 0, eta >= 1, lambda >= 0, "
+                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C), lanes in [0, %d])", fn, SMSM_MAX_OUTER,
+                   SMSM_MAX_LANES);
+    return SMSM_ERR_ARG;
+  }
+  return SMSM_OK;
+}
+
 extern "C" smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const smsm_params* params,
                                         smsm_report* report, void* stream) {
   CHECK_PLAN("smsm_reconstruct");
@@ -514,20 +533,33 @@ extern "C" smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x
   smsm_status st;
   if ((st = need_sens(plan, "smsm_reconstruct"))) return st;
   smsm_params p;
-  if (params)
-    p = *params;
-  else
-    smsm_default_params(&p);
-  if (p.outer_iters < 0 || p.outer_iters > SMSM_MAX_OUTER || p.cg_iters < 0 || p.eta < 1.0 ||
-      !(p.lambda >= 0.0) || !(p.eps0_rel > 0.0) || !(p.eps_min_rel > 0.0) ||
-      (p.mode != SMSM_MODE_IRLS && p.mode != SMSM_MODE_NULLSPACE) ||
-      (p.mode == SMSM_MODE_NULLSPACE && (p.rank <= 0 || p.rank >= plan->C)) || p.lanes < 0 ||
-      p.lanes > SMSM_MAX_LANES) {
-    smsm_set_error("smsm_reconstruct: invalid parameters (K in [0,%d], J >= 0, eta >= 1, lambda >= 0, "
-                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C), lanes in [0, %d])", SMSM_MAX_OUTER, SMSM_MAX_LANES);
+  if ((st = solve_params(plan, params, &p, "smsm_reconstruct"))) return st;
+  return solver_reconstruct(plan, y, x, &p, report, S(stream));
+}
+
+extern "C" smsm_status smsm_reconstruct_groups(int n, smsm_plan_t const* plans, const void* const* ys,
+                                               void* const* xs, const smsm_params* params, smsm_report* reports,
+                                               void* stream) {
+  if (n < 1 || !plans || !ys || !xs) {
+    smsm_set_error("smsm_reconstruct_groups: n >= 1 and the plans, ys and xs arrays are required");
     return SMSM_ERR_ARG;
   }
-  return solver_reconstruct(plan, y, x, &p, report, S(stream));
+  smsm_status st;
+  smsm_params p;
+  for (int k = 0; k < n; ++k) {
+    smsm_plan_t plan = plans[k];
+    CHECK_PLAN("smsm_reconstruct_groups");
+    CHECK_PTR("smsm_reconstruct_groups", ys[k]);
+    CHECK_PTR("smsm_reconstruct_groups", xs[k]);
+    if ((st = need_sens(plan, "smsm_reconstruct_groups"))) return st;
+    if ((st = solve_params(plan, params, &p, "smsm_reconstruct_groups"))) return st;
+    for (int j = 0; j < k; ++j)
+      if (plans[j] == plan) {
+        smsm_set_error("smsm_reconstruct_groups: plan %d appears twice (a plan holds one group's buffers)", k);
+        return SMSM_ERR_ARG;
+      }
+  }
+  return solver_reconstruct_groups(n, plans, ys, xs, &p, reports, S(stream));
 }
 
 extern "C" smsm_status smsm_sense(smsm_plan_t plan, const void* y, const void* phase, void* x, int cg_iters,

@@ -271,6 +271,8 @@ int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
                                smsm_report* report, cudaStream_t s);
 void solver_free_timing(smsm_plan_s* P);
+smsm_status solver_reconstruct_groups(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
+                                      const smsm_params* prm, smsm_report* reports, cudaStream_t s);
 smsm_status solver_sense(smsm_plan_s* P, const void* y, const void* phase, void* x, int J, smsm_report* report,
                          cudaStream_t s);
 smsm_status apply_normal_pen(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,

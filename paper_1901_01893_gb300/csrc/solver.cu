@@ -409,10 +409,8 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
 
 static bool same_params(const smsm_params* a, const smsm_params* b) { return memcmp(a, b, sizeof(*a)) == 0; }
 
-smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
-                               smsm_report* report, cudaStream_t s) {
-  const size_t nx = (size_t)P->D * P->L * P->Ns * P->N * P->N;
-  const size_t ny = (size_t)P->D * P->Ns * P->Nc * P->M * P->N;
+// Capture (once per parameter set) and instantiate the plan's solve graph.
+static smsm_status ensure_graph(smsm_plan_s* P, const smsm_params* prm) {
   if (!P->has_graph || !same_params(&P->gparams, prm)) {
     if (P->has_graph) {
       cudaGraphExecDestroy(P->gexec);
@@ -446,47 +444,88 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
     P->gparams = *prm;
     P->has_graph = 1;
   }
+  return SMSM_OK;
+}
+
+// The solve of y into x on stream s: inputs in, graph replay, result out.
+static smsm_status enqueue_run(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm, cudaStream_t s) {
+  const size_t nx = (size_t)P->D * P->L * P->Ns * P->N * P->N;
+  const size_t ny = (size_t)P->D * P->Ns * P->Nc * P->M * P->N;
   SMSM_CUDA_TRY(cudaMemcpyAsync(P->ybuf, y, sizeof(float2) * ny, cudaMemcpyDeviceToDevice, s));
   if (prm->warm) SMSM_CUDA_TRY(cudaMemcpyAsync(P->xs, x, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
   SMSM_CUDA_TRY(cudaEventRecord(P->ev0, s));
   SMSM_CUDA_TRY(cudaGraphLaunch(P->gexec, s));
   SMSM_CUDA_TRY(cudaEventRecord(P->ev1, s));
   SMSM_CUDA_TRY(cudaMemcpyAsync(x, P->xs, sizeof(float2) * nx, cudaMemcpyDeviceToDevice, s));
-  if (report) {
-    DevReport hr;
-    std::vector<SolverState> hs(P->D);
-    SMSM_CUDA_TRY(cudaMemcpyAsync(&hr, P->rep, sizeof(hr), cudaMemcpyDeviceToHost, s));
-    SMSM_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->st, sizeof(SolverState) * P->D, cudaMemcpyDeviceToHost, s));
-    SMSM_CUDA_TRY(cudaStreamSynchronize(s));
-    memset(report, 0, sizeof(*report));
-    for (int d = 0; d < P->D && !report->status; ++d) report->status = hs[d].status;
-    int flag = 0;
-    SMSM_CUDA_TRY(cudaMemcpy(&flag, P->devflag, sizeof(int), cudaMemcpyDeviceToHost));
-    if (!report->status && flag) report->status = flag;
-    report->outer_done = prm->outer_iters;
-    const int K = prm->outer_iters < SMSM_MAX_OUTER ? prm->outer_iters : SMSM_MAX_OUTER;
-    for (int k = 0; k < K; ++k) {
-      report->eps[k] = hr.eps[k];
-      report->rr_start[k] = hr.rr_start[k];
-      report->rr_end[k] = hr.rr_end[k];
-      report->sweeps[k] = hr.sweeps[k];
-    }
-    float ms = 0.f;
-    SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-    report->elapsed_ms = ms;
-    report->lanes = solve_lanes(P, prm);
-    report->lane0_batch = P->D / report->lanes;
-    report->graph_kernels = P->graph_kernels;
-    TimingPool* tp = (TimingPool*)P->tpool;
-    if (tp && prm->timing) {
-      for (size_t k = 0; k < tp->used; ++k) {
-        float t = 0.f;
-        SMSM_CUDA_TRY(cudaEventElapsedTime(&t, tp->ev[2 * k], tp->ev[2 * k + 1]));
-        report->stage_ms[tp->stage[k]] += t;
-        report->stage_launches[tp->stage[k]] += 1;
-      }
+  return SMSM_OK;
+}
+
+// Fill *report after the solve enqueued on s (synchronises s).
+static smsm_status fill_report(smsm_plan_s* P, const smsm_params* prm, smsm_report* report, cudaStream_t s) {
+  DevReport hr;
+  std::vector<SolverState> hs(P->D);
+  SMSM_CUDA_TRY(cudaMemcpyAsync(&hr, P->rep, sizeof(hr), cudaMemcpyDeviceToHost, s));
+  SMSM_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->st, sizeof(SolverState) * P->D, cudaMemcpyDeviceToHost, s));
+  SMSM_CUDA_TRY(cudaStreamSynchronize(s));
+  memset(report, 0, sizeof(*report));
+  for (int d = 0; d < P->D && !report->status; ++d) report->status = hs[d].status;
+  int flag = 0;
+  SMSM_CUDA_TRY(cudaMemcpy(&flag, P->devflag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!report->status && flag) report->status = flag;
+  report->outer_done = prm->outer_iters;
+  const int K = prm->outer_iters < SMSM_MAX_OUTER ? prm->outer_iters : SMSM_MAX_OUTER;
+  for (int k = 0; k < K; ++k) {
+    report->eps[k] = hr.eps[k];
+    report->rr_start[k] = hr.rr_start[k];
+    report->rr_end[k] = hr.rr_end[k];
+    report->sweeps[k] = hr.sweeps[k];
+  }
+  float ms = 0.f;
+  SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+  report->elapsed_ms = ms;
+  report->lanes = solve_lanes(P, prm);
+  report->lane0_batch = P->D / report->lanes;
+  report->graph_kernels = P->graph_kernels;
+  TimingPool* tp = (TimingPool*)P->tpool;
+  if (tp && prm->timing) {
+    for (size_t k = 0; k < tp->used; ++k) {
+      float t = 0.f;
+      SMSM_CUDA_TRY(cudaEventElapsedTime(&t, tp->ev[2 * k], tp->ev[2 * k + 1]));
+      report->stage_ms[tp->stage[k]] += t;
+      report->stage_launches[tp->stage[k]] += 1;
     }
   }
+  return SMSM_OK;
+}
+
+smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
+                               smsm_report* report, cudaStream_t s) {
+  smsm_status st;
+  if ((st = ensure_graph(P, prm))) return st;
+  if ((st = enqueue_run(P, y, x, prm, s))) return st;
+  return report ? fill_report(P, prm, report, s) : SMSM_OK;
+}
+
+// Independent slice groups, possibly of different geometry (one plan each), solved
+// concurrently: every plan's graph runs on the plan's own stream, forked from s and
+// joined back into it, so the kernels of small and large groups share the GPU.
+smsm_status solver_reconstruct_groups(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
+                                      const smsm_params* prm, smsm_report* reports, cudaStream_t s) {
+  smsm_status st;
+  for (int k = 0; k < n; ++k)
+    if ((st = ensure_graph(plans[k], prm))) return st;
+  cudaEvent_t fork = plans[0]->lane_ev[0];
+  SMSM_CUDA_TRY(cudaEventRecord(fork, s));
+  for (int k = 0; k < n; ++k) {
+    smsm_plan_s* P = plans[k];
+    SMSM_CUDA_TRY(cudaStreamWaitEvent(P->cap_stream, fork, 0));
+    if ((st = enqueue_run(P, ys[k], xs[k], prm, P->cap_stream))) return st;
+    SMSM_CUDA_TRY(cudaEventRecord(P->lane_ev[1], P->cap_stream));
+    SMSM_CUDA_TRY(cudaStreamWaitEvent(s, P->lane_ev[1], 0));
+  }
+  if (reports)
+    for (int k = 0; k < n; ++k)
+      if ((st = fill_report(plans[k], prm, &reports[k], s))) return st;
   return SMSM_OK;
 }
 

@@ -91,6 +91,9 @@ def lib() -> ctypes.CDLL:
     L.smsm_fft2c.restype = st
     L.smsm_sense.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(Report), vp]
     L.smsm_sense.restype = st
+    L.smsm_reconstruct_groups.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                          ctypes.POINTER(Params), ctypes.POINTER(Report), vp]
+    L.smsm_reconstruct_groups.restype = st
     L.smsm_hankel_gram_noalloc.argtypes = [vp, vp, i, i, i, i, vp]
     L.smsm_hankel_gram_noalloc.restype = st
     L.smsm_plan_device_status.argtypes = [vp, vp]
@@ -106,6 +109,21 @@ def lib() -> ctypes.CDLL:
 def _check(status: int) -> None:
     if status != SMSM_OK:
         raise SmsmError(status, lib().smsm_last_error().decode())
+
+
+def reconstruct_groups(plans, ys, params: Params | None = None, report: bool = True):
+    """Solve independent groups of possibly different geometry together (one plan each):
+    returns ([x_k], [Report_k] or None)."""
+    n = len(plans)
+    if params is None:
+        params = default_params()
+    xs = [torch.empty(p.x_shape, dtype=torch.complex64, device=y.device) for p, y in zip(plans, ys)]
+    hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+    hy = (ctypes.c_void_p * n)(*[_dev(y, p.y_shape, "y") for p, y in zip(plans, ys)])
+    hx = (ctypes.c_void_p * n)(*[_dev(x, p.x_shape, "x") for p, x in zip(plans, xs)])
+    reps = (Report * n)() if report else None
+    _check(lib().smsm_reconstruct_groups(n, hp, hy, hx, ctypes.byref(params), reps, _stream()))
+    return xs, (list(reps) if report else None)
 
 
 def default_params(**kw) -> Params:

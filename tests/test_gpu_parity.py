@@ -332,6 +332,27 @@ def test_sms_sense_parity(smsm, with_phase):
         assert err < 1e-4, err
 
 
+def test_groups_of_different_geometry_match_single_solves(smsm):
+    # Two slice groups of different geometry (64^2 MB 2 4-shot; 48^2 MB 3 2-shot)
+    # solved together on their own streams give exactly their single-plan results.
+    prm = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4)
+    plans, ys, singles = [], [], []
+    for key, seed in (("tiny", 3), ("radix3", 4)):
+        L, Ns, Nc, N, r, Ldiv = CASES[key]
+        g, xt, y = _problem(key, seed)
+        p = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv)
+        p.set_sens(c64(g["sens"]))
+        x1, rep = p.reconstruct(c64(y), params=prm)
+        assert rep.status == 0
+        plans.append(p)
+        ys.append(c64(y))
+        singles.append(x1.cpu().numpy())
+    xs, reps = smsm.reconstruct_groups(plans, ys, params=prm)
+    for k in range(len(plans)):
+        assert reps[k].status == 0
+        assert np.array_equal(xs[k].cpu().numpy(), singles[k])
+
+
 def test_lanes_give_identical_results(smsm):
     # Solving the batch as 1, 2 or 3 concurrent lanes (sub-batches on their own
     # graph branches) changes the schedule only: every direction runs the same
