@@ -212,6 +212,9 @@ smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* 
                                 int inverse, cudaStream_t s);
 smsm_status launch_rowfft_in_T(const smsm_plan_s* P, const float2* in, float2* out, int nb, int rows,
                                int inverse, cudaStream_t s);
+// inverse row FFT of p (N rows per image) with the CG update p = r + beta p fused in
+smsm_status launch_rowfft_out_T_cgp(const smsm_plan_s* P, float2* p, const float2* r, float2* out, int nb,
+                                    const double* rr_new, const double* rr_old, int nrr, cudaStream_t s);
 enum ColMode { COL_FWD = 0, COL_ADJ = 1, COL_NORMAL = 2, COL_PEN = 3 };
 // Column-stage arguments (operators.cu, colfast.cu)
 struct ColArgs {

@@ -178,6 +178,85 @@ __global__ void __launch_bounds__(256) k_rowfft_in_T(const float2* __restrict__ 
   }
 }
 
+// k_rowfft_out_T fused with the CG direction update of the previous step: the CTA
+// forms beta = <r,r>_new / <r,r>_old from the per-CTA partials of its direction (FP64,
+// fixed order), updates its rows of p in place, p = r + beta p, and transforms them.
+// Buffers are the plan's own (16-byte aligned); in[b][rows][N] -> out[b][N][rows].
+template <bool INV>
+__global__ void __launch_bounds__(256) k_rowfft_out_T_cgp(float2* __restrict__ p, const float2* __restrict__ r,
+                                                          float2* __restrict__ out, int rows, int TY, FftDesc d,
+                                                          const float2* __restrict__ tw, float sN,
+                                                          const double* __restrict__ rr_new,
+                                                          const double* __restrict__ rr_old, int nrr, int B) {
+  extern __shared__ float2 sm[];
+  __shared__ double red[2][256];
+  const int N = d.n, ld = N + 1;
+  float2* b0 = sm;
+  float2* b1 = sm + TY * ld;
+  float2* twS = b1 + TY * ld;
+  const int b = blockIdx.y, r0 = blockIdx.x * TY;
+  const size_t poff = (size_t)(b / B) * SMSM_PART_MAX;
+  double sn = 0.0, so = 0.0;
+  for (int k = threadIdx.x; k < nrr; k += blockDim.x) {
+    sn += rr_new[poff + k];
+    so += rr_old[poff + k];
+  }
+  red[0][threadIdx.x] = sn;
+  red[1][threadIdx.x] = so;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) twS[e] = tw[e];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + o];
+      red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  double beta = red[1][0] > 0.0 ? red[0][0] / red[1][0] : 0.0;
+  if (!isfinite(beta)) beta = 0.0;
+  const float bt = (float)beta;
+  float4* p4 = reinterpret_cast<float4*>(p + ((size_t)b * rows + r0) * N);
+  const float4* r4 = reinterpret_cast<const float4*>(r + ((size_t)b * rows + r0) * N);
+  const int n4 = TY * N / 2;
+  for (int e0 = threadIdx.x; e0 < n4; e0 += 4 * blockDim.x) {
+    float4 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k * blockDim.x;
+      if (e < n4) {
+        const float4 rv = __ldg(r4 + e), pv = p4[e];
+        v[k] = make_float4(fmaf(bt, pv.x, rv.x), fmaf(bt, pv.y, rv.y), fmaf(bt, pv.z, rv.z), fmaf(bt, pv.w, rv.w));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int e = e0 + k * blockDim.x;
+      if (e < n4) {
+        p4[e] = v[k];
+        const int f = 2 * e, row = f / N, col = f - row * N;  // col even: signs +, -
+        b0[row * ld + col] = cmk(v[k].x, v[k].y);
+        b0[row * ld + col + 1] = cmk(-v[k].z, -v[k].w);
+      }
+    }
+  }
+  __syncthreads();
+  float2* R = fft_smem<INV>(b0, b1, TY, ld, d, twS);
+  float2* dst = out + (size_t)b * N * rows + r0;
+  if ((TY & 1) == 0 && (rows & 1) == 0) {
+    for (int e = threadIdx.x; e < TY * N / 2; e += blockDim.x) {
+      const int col = e / (TY / 2), row = 2 * (e - col * (TY / 2));
+      const float sc = sN * sgn_par(col);
+      const float2 u = R[row * ld + col], w = R[(row + 1) * ld + col];
+      *reinterpret_cast<float4*>(dst + (size_t)col * rows + row) = make_float4(sc * u.x, sc * u.y, sc * w.x, sc * w.y);
+    }
+  } else {
+    for (int e = threadIdx.x; e < TY * N; e += blockDim.x) {
+      int col = e / TY, row = e - col * TY;
+      dst[(size_t)col * rows + row] = cscale(R[row * ld + col], sN * sgn_par(col));
+    }
+  }
+}
+
 static size_t rowfft_smem(int N, int TY) { return (size_t)(2 * TY * (N + 1) + N) * sizeof(float2); }
 
 // 16-byte vector accesses when both buffers allow them (callers' buffers may be offset)
@@ -196,6 +275,17 @@ smsm_status launch_rowfft_out_T(const smsm_plan_s* P, const float2* in, float2* 
   else
     k_rowfft_out_T<false><<<grid, 256, sm, s>>>(in, out, rows, TY, P->fN, P->twN, P->sN, vec);
   SMSM_LAUNCH_CHECK("k_rowfft_out_T");
+  return SMSM_OK;
+}
+
+smsm_status launch_rowfft_out_T_cgp(const smsm_plan_s* P, float2* p, const float2* r, float2* out, int nb,
+                                    const double* rr_new, const double* rr_old, int nrr, cudaStream_t s) {
+  const int rows = P->N;
+  const int TY = pick_ty(rows);
+  dim3 grid(rows / TY, nb);
+  k_rowfft_out_T_cgp<true><<<grid, 256, rowfft_smem(P->N, TY), s>>>(p, r, out, rows, TY, P->fN, P->twN, P->sN,
+                                                                     rr_new, rr_old, nrr, P->L * P->Ns);
+  SMSM_LAUNCH_CHECK("k_rowfft_out_T_cgp");
   return SMSM_OK;
 }
 
@@ -495,6 +585,7 @@ smsm_status operators_init_attrs() {
   SET_ATTR((k_rowfft_out_T<false>));
   SET_ATTR((k_rowfft_in_T<true>));
   SET_ATTR((k_rowfft_in_T<false>));
+  SET_ATTR((k_rowfft_out_T_cgp<true>));
 #undef SET_ATTR
   if (e != cudaSuccess) {
     smsm_set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));

@@ -206,12 +206,26 @@ __global__ void k_reset_state(SolverState* st, int D) {
 // q = (A^H A + lambda P_W) v.  With with_dots, the per-CTA partials of
 // Re<v, q> go to part_pq_col (column stage, image domain, Parseval) and
 // part_pq_band (border correction).
+// With pupd (CG steps after the first), v is first updated in place as
+// v = r + beta v, beta from the rr partial banks (fused into the x-transform).
+struct PUpdate {
+  const float2* r;
+  const double *rr_new, *rr_old;
+  int nrr;
+};
+
 static smsm_status normal_pen_timed(smsm_plan_s* P, const float2* v, float2* q, float lambda, int with_dots,
-                                    cudaStream_t s, Timer* T) {
+                                    cudaStream_t s, Timer* T, const PUpdate* pupd = nullptr) {
   const int B = P->L * P->Ns;
   smsm_status st;
   if (T) T->begin(SMSM_STAGE_ROWFFT_INV);
-  if ((st = launch_rowfft_out_T(P, v, P->hA, P->D * B, P->N, 1, s))) return st;
+  if (pupd) {
+    if ((st = launch_rowfft_out_T_cgp(P, const_cast<float2*>(v), pupd->r, P->hA, P->D * B, pupd->rr_new,
+                                      pupd->rr_old, pupd->nrr, s)))
+      return st;
+  } else if ((st = launch_rowfft_out_T(P, v, P->hA, P->D * B, P->N, 1, s))) {
+    return st;
+  }
   if (T) T->end(SMSM_STAGE_ROWFFT_INV);
   if (T) T->begin(SMSM_STAGE_COLUMN);
   if ((st = launch_col(P, COL_NORMAL, 0, P->hA, P->hB, nullptr, lambda != 0.f ? P->multT : nullptr, lambda,
@@ -334,14 +348,15 @@ static smsm_status enqueue_outer(smsm_plan_s* P, const smsm_params* prm, int k, 
   for (int j = 0; j < prm->cg_iters; ++j) {
     double* rin = (j & 1) ? rr1 : rr0;
     double* rout = (j & 1) ? rr0 : rr1;
-    if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, T))) return st;
+    // step j > 0 first completes step j-1: p = r + beta p, beta = rr(rin) / rr(rout) (the
+    // rout bank still holds the previous <r,r> until this step's update overwrites it)
+    const PUpdate pu{P->rv, rin, rout, nvb};
+    if ((st = normal_pen_timed(P, P->pv, P->qv, lam, 1, s, T, j ? &pu : nullptr))) return st;
     T->begin(SMSM_STAGE_CG);
     k_cg_update<<<vg, VEC_THREADS, 0, s>>>((float4*)P->xs, (float4*)P->rv, (const float4*)P->pv,
                                             (const float4*)P->qv, n4, P->part_pq_col, P->N, P->part_pq_band,
                                             lam != 0.f ? nbb : 0, rin, nvb, rout, P->st);
     SMSM_LAUNCH_CHECK("k_cg_update");
-    k_cg_pupdate<<<vg, VEC_THREADS, 0, s>>>((const float4*)P->rv, (float4*)P->pv, n4, rout, rin, nvb);
-    SMSM_LAUNCH_CHECK("k_cg_pupdate");
     T->end(SMSM_STAGE_CG);
   }
   double* rend = (prm->cg_iters & 1) ? rr1 : rr0;  // bank of the last write
