@@ -189,30 +189,31 @@ __global__ void __launch_bounds__(256) k_rowfft_out_T_cgp(float2* __restrict__ p
                                                           const double* __restrict__ rr_new,
                                                           const double* __restrict__ rr_old, int nrr, int B) {
   extern __shared__ float2 sm[];
-  __shared__ double red[2][256];
+  __shared__ double red[2];
   const int N = d.n, ld = N + 1;
   float2* b0 = sm;
   float2* b1 = sm + TY * ld;
   float2* twS = b1 + TY * ld;
   const int b = blockIdx.y, r0 = blockIdx.x * TY;
   const size_t poff = (size_t)(b / B) * SMSM_PART_MAX;
-  double sn = 0.0, so = 0.0;
-  for (int k = threadIdx.x; k < nrr; k += blockDim.x) {
-    sn += rr_new[poff + k];
-    so += rr_old[poff + k];
+  if (threadIdx.x < 32) {  // one warp: lane-strided sums, then a fixed butterfly
+    double sn = 0.0, so = 0.0;
+    for (int k = threadIdx.x; k < nrr; k += 32) {
+      sn += rr_new[poff + k];
+      so += rr_old[poff + k];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sn += __shfl_xor_sync(0xffffffffu, sn, o);
+      so += __shfl_xor_sync(0xffffffffu, so, o);
+    }
+    if (threadIdx.x == 0) {
+      red[0] = sn;
+      red[1] = so;
+    }
   }
-  red[0][threadIdx.x] = sn;
-  red[1][threadIdx.x] = so;
   for (int e = threadIdx.x; e < N; e += blockDim.x) twS[e] = tw[e];
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + o];
-      red[1][threadIdx.x] += red[1][threadIdx.x + o];
-    }
-    __syncthreads();
-  }
-  double beta = red[1][0] > 0.0 ? red[0][0] / red[1][0] : 0.0;
+  double beta = red[1] > 0.0 ? red[0] / red[1] : 0.0;
   if (!isfinite(beta)) beta = 0.0;
   const float bt = (float)beta;
   float4* p4 = reinterpret_cast<float4*>(p + ((size_t)b * rows + r0) * N);
