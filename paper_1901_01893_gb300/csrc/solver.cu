@@ -53,6 +53,27 @@ __device__ double sum_parts(const double* __restrict__ a, int na, const double* 
   return r;
 }
 
+// The same fixed-order sums by one warp (lane-strided, then a butterfly), both
+// results broadcast to the CTA through shared memory: one barrier instead of a tree.
+__device__ void warp_sums(const double* __restrict__ a, int na, const double* __restrict__ b, int nb,
+                          const double* __restrict__ c, int nc, double* out2) {
+  if (threadIdx.x < 32) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int k = threadIdx.x; k < na; k += 32) s0 += a[k];
+    for (int k = threadIdx.x; k < nb; k += 32) s0 += b[k];
+    for (int k = threadIdx.x; k < nc; k += 32) s1 += c[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (threadIdx.x == 0) {
+      out2[0] = s0;
+      out2[1] = s1;
+    }
+  }
+  __syncthreads();
+}
+
 __device__ void block_partial(double v, double* red, double* out) {
   red[threadIdx.x] = v;
   __syncthreads();
@@ -110,8 +131,9 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(float4* __restrict__ 
   r += off_;
   p += off_;
   q += off_;
-  const double pq = sum_parts(pq_col + poff_, ncol, pq_band + poff_, nband, red);
-  const double rr = sum_parts(rr_in + poff_, nrr, nullptr, 0, red);
+  warp_sums(pq_col + poff_, ncol, pq_band + poff_, nband, rr_in + poff_, nrr, red);
+  const double pq = red[0], rr = red[1];
+  __syncthreads();  // red is reused by the partial below
   double alpha = rr / pq;
   if (!(pq > 0.0) || !isfinite(alpha)) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && st[d_].status == 0)
