@@ -177,7 +177,7 @@ def _problem(key, seed):
     return g, xt / sc, y / sc
 
 
-@pytest.mark.parametrize("key,K,J", [("tiny", 10, 10), ("radix3", 3, 5), ("plain", 2, 3)])
+@pytest.mark.parametrize("key,K,J", [("tiny", 10, 10), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4)])
 def test_reconstruct_parity(smsm, key, K, J):
     L, Ns, Nc, N, r, Ldiv = CASES[key]
     g, xt, y = _problem(key, 1)
