@@ -207,7 +207,6 @@ class Clocks:
 TRAFFIC_PER_DIRECTION = {
     "eig": (8.663552e6 + 2.078208e6) / 26,      # profiles/k_jacobi_plain_128.md
     "gram": (27.380480e6 + 10.442496e6) / 26,   # profiles/k_gram_tc_plain_128.md
-    "band": (34.552832e6 + 0.116480e6) / 26,    # profiles/k_band_plain_128.md
     "column": (138.540544e6 + 12.339456e6) / 26,  # profiles/k_col_alias_plain_128.md
     "vapply": (38.639616e6 + 0.875264e6) / 26,  # profiles/k_vapply_plain_128.md
 }

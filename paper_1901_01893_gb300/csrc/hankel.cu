@@ -371,11 +371,14 @@ __global__ void __launch_bounds__(32 * NS) k_band(const float2* __restrict__ x, 
     for (int i = 0; i < NS; ++i) acc[p][i] = cmk(0.f, 0.f);
   {
     const float2* taps = tsm + (size_t)j * R2 * R2 * NS;
+    // tap (aa, bb) of the line is d = aa R2 + bb (horizontal strips) or bb R2 + aa
+    const int tstep = (horiz ? 1 : R2) * NS;
     for (int aa = 0; aa < R2; ++aa) {
       const float2* xr = xs + ((size_t)j * R2 + aa) * Wl + lane;
+      const float2* tp0 = taps + (size_t)(horiz ? aa * R2 : aa) * NS;
+#pragma unroll 4
       for (int bb = 0; bb < R2; ++bb) {
-        const int dd = horiz ? aa * R2 + bb : bb * R2 + aa;
-        const float2* tp = taps + (size_t)dd * NS;
+        const float2* tp = tp0 + bb * tstep;
         float2 tv[NS];
         if (NS % 2 == 0 && (ntap % 2 == 0)) {
 #pragma unroll
