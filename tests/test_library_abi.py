@@ -70,3 +70,26 @@ def test_null_plan_is_an_error(lib):
     assert lib.smsm_forward(None, None, None, None, None) == smsm.SMSM_ERR_ARG
     assert lib.smsm_reconstruct(None, None, None, None, None, None) == smsm.SMSM_ERR_ARG
     assert lib.smsm_plan_destroy(None) == smsm.SMSM_OK
+
+
+def test_group_and_sense_entry_points_check_arguments(lib):
+    from paper_1901_01893_gb300 import smsm
+
+    # no groups / missing arrays, and a NULL plan inside the list: rejected before any CUDA call
+    assert lib.smsm_reconstruct_groups(0, None, None, None, None, None, None) == smsm.SMSM_ERR_ARG
+    plans = (ctypes.c_void_p * 1)(None)
+    ys = (ctypes.c_void_p * 1)(None)
+    xs = (ctypes.c_void_p * 1)(None)
+    assert lib.smsm_reconstruct_groups(1, plans, ys, xs, None, None, None) == smsm.SMSM_ERR_ARG
+    assert lib.smsm_sense(None, None, None, None, 5, None, None) == smsm.SMSM_ERR_ARG
+
+
+def test_plan_rejects_unknown_options(lib):
+    from paper_1901_01893_gb300 import smsm
+
+    for field, value in (("boundary", 7), ("precision", 9)):
+        opts = smsm.Opts()
+        setattr(opts, field, value)
+        h = ctypes.c_void_p()
+        assert lib.smsm_plan(ctypes.byref(h), 2, 4, 8, 64, 64, 5, ctypes.byref(opts)) == smsm.SMSM_ERR_ARG
+        assert not h.value
