@@ -263,7 +263,8 @@ def run_ours(args):
     seed = seed_for_rank(cfg["seed"], rank)
     D = args.batch
     c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(dev)  # noqa: E731
-    plan = smsm.Plan(L, Ns, Nc, N, r, batch=D)
+    prec = smsm.SMSM_PRECISION_BF16_SPLIT if args.precision == "bf16-split" else smsm.SMSM_PRECISION_FP32
+    plan = smsm.Plan(L, Ns, Nc, N, r, batch=D, precision=prec)
     one = smsm.Plan(L, Ns, Nc, N, r)  # synthesis, one direction at a time
     ys = []
     for d in range(D):
@@ -385,8 +386,11 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(cfg, D), "form": "plain FP32 (FP64 reductions)",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+bf16-split",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(cfg, D),
+                   "form": ("plain FP32 (FP64 reductions)" if args.precision == "fp32" else
+                            "BF16 hi+lo split Hankel Gram, FP32 elsewhere (FP64 reductions)"),
                    "directions_per_step": D, "lanes": rep.lanes,
                    "l2": "flushed before every step (512 MB write)", "parallelism": f"replicas x{world}",
                    "lambda": LAM, "stages_ms_first_warmup": stages_all,
@@ -410,6 +414,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16-split"],
+                    help="Hankel Gram form: FP32-accurate TF32 split (default) or the BF16 hi+lo split")
     ap.add_argument("--lanes", type=int, default=0,
                     help="concurrent sub-batches of the solve (0: the library's automatic choice)")
     ap.add_argument("--batch", type=int, default=26,
