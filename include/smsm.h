@@ -248,7 +248,8 @@ smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const sms
  * captured solve (as smsm_reconstruct, same params for all) runs on that plan's
  * own stream, forked from `stream` and joined back into it, so the kernels of
  * small and large groups share the GPU.  ys[k], xs[k] are laid out as for
- * smsm_reconstruct on plans[k]; a plan may appear only once.  `reports`
+ * smsm_reconstruct on plans[k]; a plan may appear only once, and every plan must
+ * belong to the current device.  `reports`
  * (nullable) is an array of n, filled after a synchronisation of `stream`.
  */
 smsm_status smsm_reconstruct_groups(int n, smsm_plan_t const* plans, const void* const* ys, void* const* xs,

@@ -546,9 +546,16 @@ extern "C" smsm_status smsm_reconstruct_groups(int n, smsm_plan_t const* plans, 
   }
   smsm_status st;
   smsm_params p;
+  int dev = -1;
+  cudaGetDevice(&dev);
   for (int k = 0; k < n; ++k) {
     smsm_plan_t plan = plans[k];
     CHECK_PLAN("smsm_reconstruct_groups");
+    if (plan->dev != dev) {
+      smsm_set_error("smsm_reconstruct_groups: plan %d was made on device %d, the current device is %d", k,
+                     plan->dev, dev);
+      return SMSM_ERR_ARG;
+    }
     CHECK_PTR("smsm_reconstruct_groups", ys[k]);
     CHECK_PTR("smsm_reconstruct_groups", xs[k]);
     if ((st = need_sens(plan, "smsm_reconstruct_groups"))) return st;
