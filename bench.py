@@ -207,7 +207,6 @@ class Clocks:
 TRAFFIC_PER_DIRECTION = {
     "eig": (8.663552e6 + 2.078208e6) / 26,      # profiles/k_jacobi_plain_128.md
     "gram": (27.380480e6 + 10.442496e6) / 26,   # profiles/k_gram_tc_plain_128.md
-    "column": (138.540544e6 + 12.339456e6) / 26,  # profiles/k_col_alias_plain_128.md
     "vapply": (38.639616e6 + 0.875264e6) / 26,  # profiles/k_vapply_plain_128.md
 }
 
@@ -226,7 +225,7 @@ def stage_work(cfg, D, sweeps):
     lg = np.log2
     # column stage, per image column: the B lines' inverse and forward N-point FFTs
     # (5 N log2 N each), the A^H A class products (8 L Ns flops per pixel and line) and
-    # the Ns x Ns periodic multiplier (8 Ns per pixel and line)
+    # the Ns x Ns Hermitian periodic multiplier (8 Ns per pixel and line)
     col = N * (B * 2 * 5 * N * lg(N) + B * N * 8 * (L * Ns + Ns))
     return {
         "column": ("alu", D * col),
@@ -238,7 +237,9 @@ def stage_work(cfg, D, sweeps):
         "rowfft_fwd": ("hbm", D * 2 * 8 * B * NN),
         "cg": ("hbm", D * 9 * 8 * B * NN),
         "weights": ("alu", D * L * 8 * C * C * C),
-        "filters": ("alu", D * L * (R2 * R2 + 1) * Ns * Ns * R2 * R2 * r * r * 2 + D * L * Ns * Ns * NN * R2 * 8),
+        # class taps, plus the periodic multiplier's Ns(Ns+1)/2 Hermitian planes by two small DFTs
+        "filters": ("alu", D * L * (R2 * R2 + 1) * Ns * Ns * R2 * R2 * r * r * 2
+                    + D * L * (Ns * (Ns + 1) // 2) * NN * R2 * 8),
         "adjoint": ("hbm", D * 8 * (L * Nc * NN + 2 * Ns * Nc * M * N + 2 * B * NN)),
     }
 

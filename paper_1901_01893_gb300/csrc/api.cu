@@ -235,7 +235,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(Gw2, LD * C * C);
   A(wper, LD * shots * shots * R2 * R2);
   A(wcls, LD * R2 * R2 * shots * shots * R2 * R2);
-  A(multT, LD * shots * shots * NN);
+  A(multT, LD * mult_planes(shots) * NN);
   A(part_pq_col, (size_t)D * SMSM_PART_MAX);
   A(part_pq_band, (size_t)D * SMSM_PART_MAX);
   A(part_rr, (size_t)2 * D * SMSM_PART_MAX);

@@ -70,15 +70,19 @@ __device__ __forceinline__ bool alias_wait(uint64_t* mbar, uint32_t parity) {
 // partial of Re<img, acc>, and F_y back to hybrid lines.  Thread tid < N tpy
 // owns pixel row y = tid mod N of the lines b = tid / N (mod tpy); blockDim is
 // N tpy rounded up to whole warps (the extra threads only help with the FFTs).
-// Thread 0 starts TMA bulk copies of the column's B hybrid lines and (when
-// msm, i.e. they fit in shared memory) its B Ns multiplier rows as soon as the
-// CTA starts, so the HBM reads overlap the set-up and the first transform.
+// Thread 0 starts TMA bulk copies of the column's B hybrid lines as soon as the
+// CTA starts, so the HBM reads overlap the set-up.  With tpy = 1 a thread owns
+// every shot of its pixel row, and (up to 5 shots) it fetches the slice's
+// Ns(Ns+1)/2 multiplier entries (the Hermitian upper triangle) together, before
+// the class products.
 template <int L, int NS>
 __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __restrict__ corr,
-                                                   const float2* __restrict__ ash, int sh, int tpy, int msm) {
+                                                   const float2* __restrict__ ash, int sh, int tpy) {
   constexpr int B = L * NS;
+  constexpr int NPK = mult_planes(NS);
+  constexpr bool PRELOAD = NPK <= 15;  // the slice's multiplier entries fit in registers (NS <= 5)
   extern __shared__ __align__(16) float2 sm[];
-  __shared__ __align__(8) uint64_t bar[2];  // 0: hybrid lines, 1: multiplier rows
+  __shared__ __align__(8) uint64_t bar[1];  // hybrid lines
   const int N = a.N, M = a.M;
   float2* img = sm;           // [B][N]
   float2* tmp = img + B * N;  // [B][N]
@@ -86,30 +90,22 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
   float2* sTwN = ph + B * N;  // [N]
   float2* sAsh = sTwN + N;    // [NS][NS]: a_i^q, q < NS (padded to 16 bytes)
   double* red = reinterpret_cast<double*>(sAsh + ((NS * NS + 1) & ~1));  // [32]
-  float2* sM = reinterpret_cast<float2*>(red + 32);  // [B][NS][N] (msm)
   const int x = blockIdx.x;
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t NN = (size_t)N * N;
   const size_t dir = blockIdx.y;
   const float2* __restrict__ gin = a.in + dir * (size_t)B * NN;
   float2* __restrict__ gout = a.out + dir * (size_t)B * NN;
-  const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)B * NS * NN : nullptr;
+  const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)L * NPK * NN : nullptr;
   double* gdot = a.dot_part ? a.dot_part + dir * SMSM_PART_MAX : nullptr;
   const bool pen = gmult != nullptr && a.lambda != 0.f;
-  const bool use_sm = pen && msm;
   const uint32_t row_bytes = (uint32_t)(N * sizeof(float2));
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     mbar_arrive_expect_tx(&bar[0], (uint32_t)B * row_bytes);
     for (int b = 0; b < B; ++b) tma_bulk_g2s(img + b * N, gin + (size_t)b * NN + (size_t)x * N, row_bytes, &bar[0]);
-    if (use_sm) {
-      mbar_arrive_expect_tx(&bar[1], (uint32_t)(B * NS) * row_bytes);
-      for (int q = 0; q < B * NS; ++q)
-        tma_bulk_g2s(sM + q * N, gmult + (size_t)q * NN + (size_t)x * N, row_bytes, &bar[1]);
-    }
   }
   for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
   for (int e = tid; e < NS * NS; e += nt) sAsh[e] = ash[e];
@@ -133,12 +129,11 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
       bs[l][lp] = d < 0 ? d + M : d;
     }
   __syncthreads();  // barrier initialisation visible before anyone waits on it
-  // every thread agrees on the outcome of the waits, so none is left at a barrier
+  // every thread agrees on the outcome of the wait, so none is left at a barrier
   if (!__syncthreads_and(alias_wait(&bar[0], 0))) {
     if (tid == 0) {
       atomicExch(a.errflag, SMSM_ERR_TIMEOUT);
       alias_wait(&bar[0], 0);  // in-flight copies land before the CTA exits
-      if (use_sm) alias_wait(&bar[1], 0);
     }
     return;
   }
@@ -158,17 +153,11 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
     if (!own) i0 = NS;
     for (int i = i0; i < NS; i += tpy) ph[(l * NS + i) * N + y] = cmul(sAsh[i * NS + kl[l]], img[(l * NS + i) * N + y]);
   }
-  const bool mult_ok = !use_sm || alias_wait(&bar[1], 0);
-  if (!__syncthreads_and(mult_ok)) {
-    if (tid == 0) {
-      atomicExch(a.errflag, SMSM_ERR_TIMEOUT);
-      alias_wait(&bar[1], 0);  // in-flight copies land before the CTA exits
-    }
-    return;
-  }
+  __syncthreads();
 
   const float inv_ns = 1.f / (float)NS;
   const float2* cx = corr + (size_t)x * M * B * B;
+  const size_t moff = (size_t)x * N + y;
   float dsum = 0.f;
 #pragma unroll
   for (int l = 0; l < L; ++l) {
@@ -178,10 +167,9 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
 #pragma unroll
       for (int ap = 0; ap < B; ++ap) c[ap] = __ldg(crow + (size_t)ap * M);
     }
-    int i0 = (bsub - l * NS) % tpy;
-    if (i0 < 0) i0 += tpy;
-    if (!own) i0 = NS;
-    for (int i = i0; i < NS; i += tpy) {
+    const float2* ml = pen ? gmult + (size_t)l * NPK * NN : nullptr;
+    // output shot i of slice l: class product, plus lambda q (q = sum_j m_ij img_j)
+    auto emit = [&](int i, float2 q) {
       const int b = l * NS + i;
       float2 s = cmk(0.f, 0.f);
 #pragma unroll
@@ -193,21 +181,44 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
       float2 acc = cscale(cmulcj(sAsh[i * NS + kl[l]], s), inv_ns);
       const float2 v = img[b * N + y];
       if (pen) {
-        float2 q = cmk(0.f, 0.f);
-        if (use_sm) {
-          const float2* mrow = sM + b * NS * N + y;
-#pragma unroll
-          for (int j = 0; j < NS; ++j) cfma(q, mrow[j * N], img[(l * NS + j) * N + y]);
-        } else {
-          const float2* mrow = gmult + (size_t)b * NS * NN + (size_t)x * N + y;
-#pragma unroll
-          for (int j = 0; j < NS; ++j) cfma(q, mrow[(size_t)j * NN], img[(l * NS + j) * N + y]);
-        }
         acc.x = fmaf(a.lambda, q.x, acc.x);
         acc.y = fmaf(a.lambda, q.y, acc.y);
       }
       dsum = fmaf(v.x, acc.x, fmaf(v.y, acc.y, dsum));
       tmp[b * N + y] = cscale(acc, sy);
+    };
+    if (PRELOAD && tpy == 1) {
+      if (own) {
+        float2 mv[NPK];
+        if (pen) {
+#pragma unroll
+          for (int k = 0; k < NPK; ++k) mv[k] = __ldg(ml + (size_t)k * NN + moff);
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          float2 q = cmk(0.f, 0.f);
+          if (pen) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+              const float2 m = i <= j ? mv[mult_plane(i, j, NS)] : conjf2(mv[mult_plane(j, i, NS)]);
+              cfma(q, m, img[(l * NS + j) * N + y]);
+            }
+          }
+          emit(i, q);
+        }
+      }
+    } else {
+      int i0 = (bsub - l * NS) % tpy;
+      if (i0 < 0) i0 += tpy;
+      if (!own) i0 = NS;
+      for (int i = i0; i < NS; i += tpy) {
+        float2 q = cmk(0.f, 0.f);
+        if (pen) {
+#pragma unroll
+          for (int j = 0; j < NS; ++j) cfma(q, mult_at(ml, i, j, NS, NN, moff), img[(l * NS + j) * N + y]);
+        }
+        emit(i, q);
+      }
     }
   }
   // partial of Re<img, acc> (Parseval: equals Re<p, q> in k-space); FP32 over this
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(512) k_col_alias(ColArgs a, const float2* __re
   for (int b = bsub; b < B; b += tpy) gout[(size_t)b * NN + (size_t)x * N + y] = cscale(Rr[b * N + y], so);
 }
 
-typedef void (*ColAliasFn)(ColArgs, const float2*, const float2*, int, int, int);
+typedef void (*ColAliasFn)(ColArgs, const float2*, const float2*, int, int);
 
 #define CA_NS(L) {k_col_alias<L, 1>, k_col_alias<L, 2>, k_col_alias<L, 3>, k_col_alias<L, 4>, \
                   k_col_alias<L, 5>, k_col_alias<L, 6>, k_col_alias<L, 7>, k_col_alias<L, 8>}
@@ -242,24 +253,9 @@ static int alias_tpy(int N, int B) {
 
 static int alias_threads(int N, int B) { return (N * alias_tpy(N, B) + 31) / 32 * 32; }
 
-// the column's B Ns multiplier rows are staged in shared memory up to this size: off,
-// since the extra shared memory costs more occupancy than the early fetch gains
-// (measured on the plain workload: 107 us with, 98 us without, per 26-direction launch)
-#define ALIAS_MSM_MAX 0
-
-static size_t alias_smem_base(const smsm_plan_s* P) {
+static size_t alias_smem(const smsm_plan_s* P) {
   const int B = P->L * P->Ns;
   return (size_t)(3 * B * P->N + P->N + ((P->Ns * P->Ns + 1) & ~1)) * sizeof(float2) + 32 * sizeof(double);
-}
-
-static size_t alias_msm_bytes(const smsm_plan_s* P) {
-  return (size_t)P->L * P->Ns * P->Ns * P->N * sizeof(float2);
-}
-
-static int alias_msm(const smsm_plan_s* P) { return alias_msm_bytes(P) <= ALIAS_MSM_MAX; }
-
-static size_t alias_smem(const smsm_plan_s* P) {
-  return alias_smem_base(P) + (alias_msm(P) ? alias_msm_bytes(P) : 0);
 }
 
 size_t alias_corr_count(const smsm_plan_s* P) {
@@ -296,7 +292,7 @@ smsm_status launch_alias_corr(const smsm_plan_s* P, cudaStream_t s) {
 smsm_status launch_col_alias(const smsm_plan_s* P, const ColArgs& a, cudaStream_t s) {
   const int tpy = alias_tpy(P->N, P->L * P->Ns);
   kColAlias[P->L - 1][P->Ns - 1]<<<dim3(P->N, P->D), alias_threads(P->N, P->L * P->Ns), alias_smem(P), s>>>(
-      a, P->acorr, P->ash, P->N / P->Ldiv, tpy, alias_msm(P));
+      a, P->acorr, P->ash, P->N / P->Ldiv, tpy);
   SMSM_LAUNCH_CHECK("k_col_alias");
   return SMSM_OK;
 }

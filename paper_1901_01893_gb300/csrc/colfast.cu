@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_col_fast(ColArgs a) {
   const size_t dir = blockIdx.y;
   const float2* __restrict__ gin = a.in + dir * (size_t)B * NN;
   float2* __restrict__ gout = a.out + dir * (size_t)B * NN;
-  const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)B * Ns * NN : nullptr;
+  const float2* __restrict__ gmult = a.multT ? a.multT + dir * (size_t)L * mult_planes(Ns) * NN : nullptr;
   double* gdot = a.dot_part ? a.dot_part + dir * SMSM_PART_MAX : nullptr;
   for (int e = tid; e < N; e += nt) sTwN[e] = a.twN[e];
   for (int e = tid; e < M; e += nt) sTwM[e] = a.twM[e];
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(256) k_col_fast(ColArgs a) {
       const int y = lane + 32 * k;
       float2 s = cmk(0.f, 0.f);
       if (pen) {
-        for (int j = 0; j < Ns; ++j)
-          cfma(s, gmult[(size_t)((l * Ns + i) * Ns + j) * NN + (size_t)x * N + y], img[(l * Ns + j) * N + y]);
+        const float2* ml = gmult + (size_t)l * mult_planes(Ns) * NN;
+        for (int j = 0; j < Ns; ++j) cfma(s, mult_at(ml, i, j, Ns, NN, (size_t)x * N + y), img[(l * Ns + j) * N + y]);
         s = cscale(s, a.lambda);
       }
       acc[l][k] = s;

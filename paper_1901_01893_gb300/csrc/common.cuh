@@ -39,6 +39,19 @@ __device__ __forceinline__ void cfmacj(float2& acc, float2 a, float2 b) {
 }
 
 // asynchronous 8-byte global -> shared copy (completes at cp_async_wait_all)
+// Periodic penalty multiplier m_ii'[x][y] of one (direction, slice).  It is
+// Hermitian in the shot pair (wt_ii'[d] = conj(wt_i'i[-d]) because W is), so only
+// the upper triangle i <= i' is stored, in Ns(Ns+1)/2 planes [pk][x][y] with
+// pk = i Ns - i(i-1)/2 + (i' - i); the lower entries are the conjugates.
+__host__ __device__ constexpr int mult_planes(int Ns) { return Ns * (Ns + 1) / 2; }
+__host__ __device__ constexpr int mult_plane(int i, int j, int Ns) { return i * Ns - i * (i - 1) / 2 + (j - i); }
+// m_ij at offset off of a plane; m points at the slice's first plane
+__device__ __forceinline__ float2 mult_at(const float2* __restrict__ m, int i, int j, int Ns, size_t NN, size_t off) {
+  if (i <= j) return __ldg(m + (size_t)mult_plane(i, j, Ns) * NN + off);
+  const float2 v = __ldg(m + (size_t)mult_plane(j, i, Ns) * NN + off);
+  return cmk(v.x, -v.y);
+}
+
 __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
                "l"(src)
@@ -123,7 +136,7 @@ struct smsm_plan_s {
   float2 *Gw, *Gw2;  // [LD][C][C] warm-start congruence V^H G V (and its half product)
   float2* wper;      // [L][Ns][Ns][R2*R2]
   float2* wcls;      // [LD][R2*R2 classes][Ns (i')][R2*R2 taps][Ns (i)] border correction taps
-  float2* multT;     // [L][Ns][Ns][N(x)][N(y)]
+  float2* multT;     // [L][Ns(Ns+1)/2][N(x)][N(y)]: upper triangle of the Hermitian shot coupling
   double *part_pq_col, *part_pq_band, *part_rr;  // partial sums [D][PART]; part_rr: [2 banks][D][PART]
   SolverState* st;   // [D]
   DevReport* rep;
@@ -222,7 +235,7 @@ struct ColArgs {
   float2* out;
   const float2* sensT;   // [L][Nc][x][y]
   const float2* phaseT;  // [L][Ns][x][y]
-  const float2* multT;   // [L][Ns][Ns][x][y]
+  const float2* multT;   // [L][Ns(Ns+1)/2][x][y] (upper triangle, see mult_at)
   const float2* twN;
   const float2* twM;
   const float2* tw_shot;  // [Ns][N]

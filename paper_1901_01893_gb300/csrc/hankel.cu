@@ -239,7 +239,8 @@ __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, f
 
 static size_t filters_smem(const smsm_plan_s* P) { return (size_t)P->r * P->r * (P->C + 1) * sizeof(float2); }
 
-// multT[l][i][i'][x][y] = sum_dy E[dy][y] sum_dx wt[dy][dx] E[dx][x],  E[d][n] = exp(-j 2 pi (d-(r-1)) (n - N/2)/N)
+// multT[l][pk(i,i')][x][y] = sum_dy E[dy][y] sum_dx wt_ii'[dy][dx] E[dx][x],  E[d][n] = exp(-j 2 pi (d-(r-1)) (n - N/2)/N),
+// for i <= i' only (the multiplier is Hermitian in the shot pair); the diagonal planes are real.
 #define MULT_XB 8
 __global__ void __launch_bounds__(256) k_mult(const float2* __restrict__ wper, const float2* __restrict__ E,
                                               float2* __restrict__ multT, int Ns, int N, int r) {
@@ -247,8 +248,11 @@ __global__ void __launch_bounds__(256) k_mult(const float2* __restrict__ wper, c
   __shared__ float2 wt[23 * 23];
   __shared__ float2 T[23][MULT_XB];
   const int x0 = blockIdx.x * MULT_XB;
-  const int ij = blockIdx.y, l = blockIdx.z;
-  const size_t fb = ((size_t)l * Ns * Ns + ij);
+  const int pk = blockIdx.y, l = blockIdx.z;
+  int i = 0;
+  while (mult_plane(i + 1, i + 1, Ns) <= pk) ++i;
+  const int j = i + (pk - mult_plane(i, i, Ns));
+  const size_t fb = (size_t)l * Ns * Ns + (size_t)i * Ns + j;
   for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) wt[e] = wper[fb * R2 * R2 + e];
   __syncthreads();
   for (int e = threadIdx.x; e < R2 * MULT_XB; e += blockDim.x) {
@@ -259,12 +263,13 @@ __global__ void __launch_bounds__(256) k_mult(const float2* __restrict__ wper, c
     T[dy][xl] = s;
   }
   __syncthreads();
-  float2* out = multT + fb * (size_t)N * N;
+  float2* out = multT + ((size_t)l * mult_planes(Ns) + pk) * N * N;
   for (int e = threadIdx.x; e < MULT_XB * N; e += blockDim.x) {
     int xl = e / N, y = e - xl * N;
     if (x0 + xl >= N) continue;
     float2 s = cmk(0.f, 0.f);
     for (int dy = 0; dy < R2; ++dy) cfma(s, E[(size_t)dy * N + y], T[dy][xl]);
+    if (i == j) s.y = 0.f;
     out[(size_t)(x0 + xl) * N + y] = s;
   }
 }
@@ -284,7 +289,7 @@ smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s
   k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C,
                                                               !P->periodic);  // wcls holds the class taps dcls
   SMSM_LAUNCH_CHECK("k_filters");
-  dim3 g2((P->N + MULT_XB - 1) / MULT_XB, P->Ns * P->Ns, P->LD);
+  dim3 g2((P->N + MULT_XB - 1) / MULT_XB, mult_planes(P->Ns), P->LD);
   k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
   SMSM_LAUNCH_CHECK("k_mult");
   return SMSM_OK;

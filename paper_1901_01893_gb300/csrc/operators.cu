@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_col(const ColArgs a_param) {
     else
       a.out += d * (size_t)((MODE == COL_ADJ && PHASE) ? L : B) * NN;
     if (a.phaseT) a.phaseT += d * (size_t)B * NN;
-    if (a.multT) a.multT += d * (size_t)B * Ns * NN;
+    if (a.multT) a.multT += d * (size_t)L * mult_planes(Ns) * NN;
     if (a.dot_part) a.dot_part += d * SMSM_PART_MAX;
   }
 
@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(COL_THREADS) k_col(const ColArgs a_param) {
       if (pen) {
         int b = e / N, y = e - b * N;
         int l = b / Ns, i = b - l * Ns;
-        for (int j = 0; j < Ns; ++j)
-          cfma(s, a.multT[(size_t)((l * Ns + i) * Ns + j) * NN + (size_t)x * N + y], img[(l * Ns + j) * N + y]);
+        const float2* ml = a.multT + (size_t)l * mult_planes(Ns) * NN;
+        for (int j = 0; j < Ns; ++j) cfma(s, mult_at(ml, i, j, Ns, NN, (size_t)x * N + y), img[(l * Ns + j) * N + y]);
         s = cscale(s, a.lambda);
       }
       acc[e] = s;

@@ -305,7 +305,7 @@ static smsm_plan_s lane_view(const smsm_plan_s* P, int d0, int nd, int lane) {
   v.sweeps += dd * L;
   v.wper += dd * L * Ns * Ns * R2 * R2;
   v.wcls += dd * L * R2 * R2 * Ns * Ns * R2 * R2;
-  v.multT += dd * L * Ns * Ns * NN;
+  v.multT += dd * L * mult_planes(Ns) * NN;
   v.part_pq_col += dd * SMSM_PART_MAX;
   v.part_pq_band += dd * SMSM_PART_MAX;
   v.part_rr += 2 * dd * SMSM_PART_MAX;
