@@ -197,6 +197,21 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
       __syncthreads();
     }
     if (!__syncthreads_or(rotated)) break;
+    // A sweep that sets no rotation changes nothing, and it sets none exactly when no
+    // pair passes the rotation test on the current matrix: test every pair directly
+    // (same arithmetic as the rotation step) instead of running that sweep.
+    int need = 0;
+    for (int e = tid; e < Cp * Cp && !need; e += nt) {
+      const int p = e / Cp, q = e - p * Cp;
+      if (p >= q) continue;
+      const float2 b = g[p * ld + q];
+      const float babs = hypotf(b.x, b.y);
+      need = babs > floor_abs && babs > tol * sqrtf(fabsf(g[p * ld + p].x * g[q * ld + q].x));
+    }
+    if (!__syncthreads_or(need)) {
+      ++sw;
+      break;
+    }
   }
   for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
