@@ -57,6 +57,8 @@ CASES = {
     "odd_shots": (1, 3, 4, 96, 3, 1),  # Ns = 3, M = 32, one slice
     "mb3_8shots": (3, 8, 6, 64, 3, 3),  # M = 8, C = 72
     "r1": (2, 2, 3, 32, 1, 2),         # filter 1: C = Ns
+    "maxc": (2, 2, 4, 64, 9, 2),       # largest C the eigensolver takes: C = Cp = 162 (FMA Gram)
+    "maxn": (1, 2, 2, 512, 2, 1),      # largest image edge, N = 512
 }
 
 
@@ -99,7 +101,7 @@ def test_forward_adjoint_phase_mode(smsm, key):
     assert O.nrmse(xg, O.adjoint(y, S, L, Ldiv=Ldiv, phase=ph)) < OP_TOL
 
 
-@pytest.mark.parametrize("key", ["tiny", "precision", "radix3"])
+@pytest.mark.parametrize("key", ["tiny", "precision", "radix3", "maxn"])
 def test_fft2c_parity(smsm, key):
     plan, S, rng = make_plan(smsm, key)
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -110,7 +112,7 @@ def test_fft2c_parity(smsm, key):
     assert O.nrmse(back, img) < OP_TOL
 
 
-@pytest.mark.parametrize("key", ["tiny", "plain", "radix3", "mb3_8shots", "r1"])
+@pytest.mark.parametrize("key", ["tiny", "plain", "radix3", "mb3_8shots", "r1", "maxc", "maxn"])
 def test_gram_parity(smsm, key):
     plan, S, rng = make_plan(smsm, key)
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -145,7 +147,7 @@ def _random_weight(rng, L, C):
     return (A + np.conj(np.swapaxes(A, 1, 2))) / np.sqrt(C)
 
 
-@pytest.mark.parametrize("key", ["tiny", "plain", "precision", "radix3", "mb3_8shots", "r1"])
+@pytest.mark.parametrize("key", ["tiny", "plain", "precision", "radix3", "mb3_8shots", "r1", "maxc", "maxn"])
 def test_apply_filters_parity(smsm, key):
     plan, S, rng = make_plan(smsm, key)
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -177,7 +179,8 @@ def _problem(key, seed):
     return g, xt / sc, y / sc
 
 
-@pytest.mark.parametrize("key,K,J", [("tiny", 10, 10), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4)])
+@pytest.mark.parametrize("key,K,J", [("tiny", 10, 10), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4),
+                                     ("maxc", 2, 3), ("maxn", 2, 3)])
 def test_reconstruct_parity(smsm, key, K, J):
     L, Ns, Nc, N, r, Ldiv = CASES[key]
     g, xt, y = _problem(key, 1)
