@@ -5,22 +5,25 @@
 // The columns are padded to Cp = 16*ceil(C/16), so X has 2Cp columns: Re in
 // [0, Cp), Im in [Cp, 2Cp).
 //
-// One CTA computes a 128-row tile t of R against all 2Cp columns (two MMAs of
-// N = Cp) over a contiguous block of patch rows ky (split-K); its FP32 partial
-// goes to global memory and k_gram_tc_reduce adds the partials in FP64 in a
-// fixed order.  Roles (warp-specialised, 288 threads):
+// Only R's upper triangle is needed (R is symmetric and G reads entries with
+// row <= column), so one CTA computes, from one staged copy of X^T, every
+// 128-row tile t of R against the columns [128 t, 2Cp): tile 0 as two MMAs of
+// N = Cp, the others as one MMA of N = 2Cp - 128 t (480 TMEM columns at
+// 2Cp = 288).  It covers a contiguous block of patch rows ky (split-K); its FP32
+// partial goes to global memory and k_gram_tc_reduce adds the partials in FP64
+// in a fixed order.  Roles (warp-specialised, 352 threads):
 //   * thread 0 brings the window of patch row ky -- image rows ky..ky+r-1 of
 //     every shot -- into shared memory with TMA bulk copies (two windows in
 //     flight, completion counted on an mbarrier);
-//   * warps 0-3 build each chunk of KCH patches (32 bytes along K) from the
+//   * the producer warps build each chunk of KCH patches (32 bytes along K) from the
 //     window (implicit im2col), split every value into hi + lo and write X^T
 //     (all 2Cp rows, hi and lo) into a 3-stage ring in the canonical K-major
 //     layout;
-//   * one thread of warp 8 issues  D += Xh_t Xh^T + Xh_t Xl^T + Xl_t Xh^T
-//     (the A tile is a row window of the same staged X^T) and commits each
-//     stage back to its producers;
-//   * warps 4-7 drain the TMEM accumulator every GTC_EPOCH chunks into the
-//     CTA's FP32 partial in global memory (each thread owns one row and adds
+//   * one thread of the last warp issues  D_t += Xh_t Xh_c^T + Xh_t Xl_c^T +
+//     Xl_t Xh_c^T  for every tile t (A and B are row windows of the same staged
+//     X^T) and commits each stage back to its producers;
+//   * four warps drain the TMEM accumulator every GTC_EPOCH chunks into the
+//     CTA's FP32 partial in global memory (each thread owns one row per tile and adds
 //     with fire-and-forget reductions), which bounds the error
 //     that the tensor core's FP32 accumulation gathers over many chunks.
 //   precision 0: TF32 split (hi = x with the low 13 mantissa bits cleared,
@@ -30,6 +33,8 @@
 // plan's device error flag, lets its in-flight bulk copies and MMAs finish
 // (bounded waits), frees TMEM and returns.
 #include <cuda_bf16.h>
+
+#include <cmath>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -79,7 +84,18 @@ __host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp, in
   return L;
 }
 
-// This CTA: row tile t of R, patch rows ky in [ky0, ky1) (block g of nG), matrix lf.
+// TMEM columns of one CTA: the row tiles' accumulators side by side, tile t holding
+// the columns [128 t, 2Cp) -- sum_t (2Cp - 128 t) -- rounded up to a power of two >= 32
+// (480 of 512 at 2Cp = 288).
+__host__ __device__ inline int gtc_tmem_cols(int R2C) {
+  const int ntile = (R2C + 127) / 128;
+  const int need = ntile * R2C - 64 * ntile * (ntile - 1);
+  int c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+// This CTA: every row tile of R, patch rows ky in [ky0, ky1) (block g of nG), matrix lf.
 // A chunk is KCH = 32 GTC_KSTEP / ESZ consecutive patches of one patch row (the row's
 // tail zero-padded).  Producer unit = one 16-byte core-matrix row: column c of X (its
 // Re and Im rows of X^T), EPC consecutive patches.
@@ -99,10 +115,11 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   __shared__ __align__(8) uint64_t full_b[3], empty_b[3], accfull_b, accempty_b, win_b[2], fin_b;
   __shared__ volatile int s_abort;
 
-  const int t = blockIdx.x, g = blockIdx.y, lf = blockIdx.z;
+  const int g = blockIdx.x, lf = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R2C = 2 * Cp;
   const GtcLayout Lo = gtc_layout(Ns, N, r, Cp, periodic);
+  const int ntile = Lo.rows_alloc / 128;
   const int NST = Lo.nst;
   const size_t arr_bytes = Lo.arr_bytes;
   const int WP = Lo.wp;
@@ -114,10 +131,8 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const int rr = r * r;
   const size_t NN = (size_t)N * N;
   const float2* xl = x + (size_t)lf * Ns * NN;
-  const bool need_h0 = Cp > 128 * t;  // columns [0, Cp) reach the upper triangle of this row tile
-  const int c_begin = need_h0 ? 0 : Cp;
   const uint32_t win_bytes = (uint32_t)((size_t)Ns * r * (N + Lo.ext) * sizeof(float2));
-  const int tmem_cols = R2C > 256 ? 512 : 256;
+  const int tmem_cols = gtc_tmem_cols(R2C);
 
   for (size_t e = tid; e < 2 * NST * arr_bytes / 16; e += GTC_THREADS)
     reinterpret_cast<uint4*>(gsm)[e] = make_uint4(0, 0, 0, 0);
@@ -264,7 +279,6 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
       for (int w = consumed; w < issued; ++w) mbar_wait(&win_b[w & 1], (uint32_t)((w >> 1) & 1), GTC_MAXITER);
   } else if (tid == 32 * (GTC_PROD_WARPS + 4)) {
     // ---------------- MMA issue (one thread, in a warp of its own) ----------------
-    const uint32_t idesc = umma_idesc(PREC == 0 ? 2u : 1u, 128, Cp);
     for (int it = 0; it < nit; ++it) {
       const int s = it % NST;
       if (!gtc_wait(&full_b[s], (uint32_t)((it / NST) & 1), &s_abort)) break;
@@ -272,26 +286,35 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
       if (it % GTC_EPOCH == 0 && ep > 0 && !gtc_wait(&accempty_b, (uint32_t)((ep - 1) & 1), &s_abort)) break;
       tc_fence_after();
       const uint32_t hb = smem_u32(gsm + (size_t)s * 2 * arr_bytes), lb = hb + (uint32_t)arr_bytes;
-      const uint32_t arow = (uint32_t)(128 * t / 8) * SBO;
 #pragma unroll
       for (int ks = 0; ks < GTC_KSTEP; ++ks) {
         const uint32_t kb = (uint32_t)ks * 2 * LBO;
-        const uint64_t ah = umma_desc(hb + arow + kb, LBO, SBO), al = umma_desc(lb + arow + kb, LBO, SBO);
         // a new epoch overwrites the accumulator
         const uint32_t acc0 = (it % GTC_EPOCH || ks) ? 1u : 0u;
-        for (int h = need_h0 ? 0 : 1; h < 2; ++h) {
-          const uint32_t brow = (uint32_t)(h * Cp / 8) * SBO + kb;
-          const uint64_t bh = umma_desc(hb + brow, LBO, SBO), bl = umma_desc(lb + brow, LBO, SBO);
-          const uint32_t d = tmem + (uint32_t)(h * Cp);
-          if (PREC == 0) {
-            umma_tf32(d, ah, bh, idesc, acc0);
-            umma_tf32(d, ah, bl, idesc, 1u);
-            umma_tf32(d, al, bh, idesc, 1u);
-          } else {
-            umma_bf16(d, ah, bh, idesc, acc0);
-            umma_bf16(d, ah, bl, idesc, 1u);
-            umma_bf16(d, al, bh, idesc, 1u);
+        uint32_t toff = 0;  // TMEM column of tile tt's first accumulator column
+        for (int tt = 0; tt < ntile; ++tt) {
+          const uint32_t arow = (uint32_t)(16 * tt) * SBO;  // rows 128 tt .. of X^T
+          const uint64_t ah = umma_desc(hb + arow + kb, LBO, SBO), al = umma_desc(lb + arow + kb, LBO, SBO);
+          const int w = R2C - 128 * tt;                      // columns [128 tt, 2Cp)
+          const int np = (tt == 0 && w > 256) ? 2 : 1;       // N <= 256 per MMA
+          const int pw = w / np;
+          const uint32_t idesc = umma_idesc(PREC == 0 ? 2u : 1u, 128, pw);
+          for (int pc = 0; pc < np; ++pc) {
+            const int c0 = 128 * tt + pc * pw;
+            const uint32_t brow = (uint32_t)(c0 / 8) * SBO + kb;
+            const uint64_t bh = umma_desc(hb + brow, LBO, SBO), bl = umma_desc(lb + brow, LBO, SBO);
+            const uint32_t d = tmem + toff + (uint32_t)(pc * pw);
+            if (PREC == 0) {
+              umma_tf32(d, ah, bh, idesc, acc0);
+              umma_tf32(d, ah, bl, idesc, 1u);
+              umma_tf32(d, al, bh, idesc, 1u);
+            } else {
+              umma_bf16(d, ah, bh, idesc, acc0);
+              umma_bf16(d, ah, bl, idesc, 1u);
+              umma_bf16(d, al, bh, idesc, 1u);
+            }
           }
+          toff += (uint32_t)w;
         }
       }
       umma_commit(&empty_b[s]);
@@ -303,33 +326,45 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   } else if (warp >= GTC_PROD_WARPS && warp < GTC_PROD_WARPS + 4) {
     // ---------------- drain: each epoch's accumulator into this CTA's FP32 partial (L2) ----------------
     const int lw = warp & 3;  // TMEM lanes 32 (warp % 4) .. +31 are this warp's
-    const int row = 128 * t + 32 * lw + lane;
-    float* orow = Rpart + ((size_t)lf * nG + g) * R2C * R2C + (size_t)row * R2C;
+    float* Rl = Rpart + ((size_t)lf * nG + g) * R2C * R2C;
     for (int ep = 0; ep < nepoch; ++ep) {
       // warp-uniform: the TMEM loads below are .sync.aligned
       if (!__all_sync(0xffffffffu, gtc_wait(&accfull_b, (uint32_t)(ep & 1), &s_abort))) break;
       tc_fence_after();
       // the first epoch stores, later ones add without reading back (no round trip to L2)
-      for (int c0 = c_begin; c0 < R2C; c0 += 16) {
-        uint32_t dv[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * lw) << 16) + (uint32_t)c0, dv);
-        if (row < R2C) {
+      uint32_t toff = 0;
+      for (int tt = 0; tt < ntile; ++tt) {
+        const int w = R2C - 128 * tt;
+        const int row = 128 * tt + 32 * lw + lane;
+        if (128 * tt + 32 * lw < R2C) {  // warp-uniform: some row of this warp is in range
+          float* orow = Rl + (size_t)row * R2C + 128 * tt;
+          for (int c0 = 0; c0 < w; c0 += 16) {
+            uint32_t dv[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * lw) << 16) + toff + (uint32_t)c0, dv);
+            if (row < R2C) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float v0 = __uint_as_float(dv[4 * q]), v1 = __uint_as_float(dv[4 * q + 1]);
-            const float v2 = __uint_as_float(dv[4 * q + 2]), v3 = __uint_as_float(dv[4 * q + 3]);
-            if (ep == 0)
-              *reinterpret_cast<float4*>(orow + c0 + 4 * q) = make_float4(v0, v1, v2, v3);
-            else
-              red_add_v4(orow + c0 + 4 * q, v0, v1, v2, v3);
+              for (int q = 0; q < 4; ++q) {
+                const float v0 = __uint_as_float(dv[4 * q]), v1 = __uint_as_float(dv[4 * q + 1]);
+                const float v2 = __uint_as_float(dv[4 * q + 2]), v3 = __uint_as_float(dv[4 * q + 3]);
+                if (ep == 0)
+                  *reinterpret_cast<float4*>(orow + c0 + 4 * q) = make_float4(v0, v1, v2, v3);
+                else
+                  red_add_v4(orow + c0 + 4 * q, v0, v1, v2, v3);
+              }
+            }
           }
         }
+        toff += (uint32_t)w;
       }
       tc_fence_before();
       mbar_arrive(&accempty_b);
     }
-    if (nepoch == 0 && row < R2C)
-      for (int c = c_begin; c < R2C; ++c) orow[c] = 0.f;
+    if (nepoch == 0)
+      for (int tt = 0; tt < ntile; ++tt) {
+        const int row = 128 * tt + 32 * lw + lane;
+        if (row < R2C)
+          for (int c = 128 * tt; c < R2C; ++c) Rl[(size_t)row * R2C + c] = 0.f;
+      }
   }
   __syncthreads();
   if (s_abort && tid == 0) atomicExch(errflag, SMSM_ERR_TIMEOUT);
@@ -338,8 +373,9 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   if (warp == 0) tmem_dealloc(tmem, tmem_cols);
 }
 
-// G[c][c'] (c <= c') = sum_g (R[c][c'] + R[Cp+c][Cp+c']) + i (R[c][Cp+c'] - R[c'][Cp+c]) in FP64;
-// the lower triangle is the conjugate, so G is exactly Hermitian.
+// G[c][c'] (c <= c') = sum_g (R[c][c'] + R[Cp+c][Cp+c']) + i (R[c][Cp+c'] - R[c'][Cp+c]) in FP64,
+// every entry read from R's upper triangle; G[c'][c] is written as the conjugate, so G is
+// exactly Hermitian.
 __global__ void k_gram_tc_reduce(const float* __restrict__ Rpart, double2* __restrict__ G, int LD, int C, int Cp,
                                  int nG) {
   const int R2C = 2 * Cp;
@@ -347,17 +383,21 @@ __global__ void k_gram_tc_reduce(const float* __restrict__ Rpart, double2* __res
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int lf = (int)(e / ((size_t)C * C));
     const int rem = (int)(e - (size_t)lf * C * C);
-    const int a = rem / C, b = rem - a * C;
-    const int c = a <= b ? a : b, cc = a <= b ? b : a;
+    const int c = rem / C, cc = rem - c * C;
+    if (c > cc) continue;
     double re = 0.0, im = 0.0;
     for (int g = 0; g < nG; ++g) {
       const float* R = Rpart + ((size_t)lf * nG + g) * R2C * R2C;
       re += (double)R[(size_t)c * R2C + cc] + (double)R[(size_t)(Cp + c) * R2C + Cp + cc];
       im += (double)R[(size_t)c * R2C + Cp + cc] - (double)R[(size_t)cc * R2C + Cp + c];
     }
-    if (a > b) im = -im;
-    if (a == b) im = 0.0;
-    G[e] = make_double2(re, im);
+    double2* Gl = G + (size_t)lf * C * C;
+    if (c == cc) {
+      Gl[(size_t)c * C + c] = make_double2(re, 0.0);
+    } else {
+      Gl[(size_t)c * C + cc] = make_double2(re, im);
+      Gl[(size_t)cc * C + c] = make_double2(re, -im);
+    }
   }
 }
 
@@ -365,22 +405,34 @@ static size_t gram_tc_smem_for(int C, int Ns, int r, int N, int periodic) {
   return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16), periodic).total;
 }
 
-// 2Cp <= 288 TMEM columns; the ring and two patch-row windows in shared memory
+// 2Cp <= 288: the row tiles' accumulators take at most 480 TMEM columns; the ring and two
+// patch-row windows in shared memory
 int gram_tc_supported(const smsm_plan_s* P) {
   return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic) <= 224 * 1024;
 }
 
 int gram_tc_cp(const smsm_plan_s* P) { return 16 * ((P->C + 15) / 16); }
 
-// blocks of patch rows per (row tile, matrix): about four waves over 152 SMs when the
-// batch is large, more blocks (down to 2 patch rows each) when it is small
+// blocks of patch rows per matrix (split-K): between two and four waves of CTAs over the
+// 152 SMs, the count whose last wave is fullest; more blocks (down to 2 patch rows each)
+// when the batch is small; the FP32 partials stay under 256 MB
 int gram_tc_nG(const smsm_plan_s* P) {
   const int Cp = gram_tc_cp(P), R2C = 2 * Cp;
-  const int ntile = (R2C + 127) / 128;
-  int nG = (4 * 152 + ntile * P->LD - 1) / (ntile * P->LD);
+  const int LD = P->LD, nsm = 152;
+  const int lo = (2 * nsm + LD - 1) / LD, hi = (4 * nsm + LD - 1) / LD;
+  int nG = lo;
+  double best = -1.0;
+  for (int n = lo; n <= hi; ++n) {
+    const double waves = (double)LD * n / nsm;
+    const double fill = waves / std::ceil(waves);
+    if (fill > best + 1e-9) {
+      best = fill;
+      nG = n;
+    }
+  }
   const int most = (P->P1 + 1) / 2;
   if (nG > most) nG = most;
-  const size_t per = (size_t)P->LD * R2C * R2C * sizeof(float);
+  const size_t per = (size_t)LD * R2C * R2C * sizeof(float);
   int cap = (int)((size_t)256 * 1024 * 1024 / per);
   if (cap < 1) cap = 1;
   if (nG > cap) nG = cap;
@@ -404,10 +456,9 @@ smsm_status gram_tc_init_attrs() {
 }
 
 smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s) {
-  const int Cp = gram_tc_cp(P), R2C = 2 * Cp;
-  const int ntile = (R2C + 127) / 128;
+  const int Cp = gram_tc_cp(P);
   const int nG = P->gram_tc_nG;
-  dim3 grid(ntile, nG, P->LD);
+  dim3 grid(nG, P->LD);
   if (P->precision == SMSM_PRECISION_BF16_SPLIT)
     k_gram_tc<1><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
                                                                  nG, P->P1, P->periodic);

@@ -158,6 +158,22 @@ def test_apply_filters_parity(smsm, key):
     assert O.nrmse(out, ref) < OP_TOL
 
 
+@pytest.mark.parametrize("key", ["tiny", "radix3", "mb3_8shots"])
+def test_apply_filters_is_self_adjoint(smsm, key):
+    # Hermitian W: <P x, y> = <x, P y>.  The periodic multiplier is stored as the upper
+    # triangle of a Hermitian shot coupling, so only rounding separates the two sides.
+    plan, S, rng = make_plan(smsm, key)
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    x = crandn(rng, L, Ns, N, N).astype(np.complex64)
+    y = crandn(rng, L, Ns, N, N).astype(np.complex64)
+    W = _random_weight(rng, L, Ns * r * r)
+    px = plan.apply_filters(c128(W), c64(x)).cpu().numpy().astype(np.complex128)
+    py = plan.apply_filters(c128(W), c64(y)).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(px, y.astype(np.complex128))
+    rhs = np.vdot(x.astype(np.complex128), py)
+    assert abs(lhs - rhs) < 1e-5 * np.linalg.norm(px) * np.linalg.norm(y)
+
+
 def test_apply_filters_identity_weight(smsm):
     # W = I: the penalty is the patch-count map c(n) times x (closed form)
     plan, S, rng = make_plan(smsm, "radix3")

@@ -243,6 +243,24 @@ def test_penalty_with_identity_weight():
     assert np.allclose(O.penalty(x, W, r), np.outer(c1, c1) * x, atol=1e-12)
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_penalty_is_self_adjoint_for_hermitian_weight(periodic):
+    # P_W = H^* (H(.) W) with W Hermitian: <P_W x, y> = tr((Hy)^H (Hx) W) = <x, P_W y>.
+    # The image-domain shot coupling m_ii' of the periodic part is then Hermitian in
+    # (i, i'), which is what lets the GPU store only its upper triangle.
+    L, Ns, N, r = 2, 3, 12, 3
+    x, y = crandn(L, Ns, N, N), crandn(L, Ns, N, N)
+    W = _random_hermitian(L, Ns * r * r)
+    lhs = np.vdot(O.penalty(x, W, r, periodic=periodic), y)
+    rhs = np.vdot(x, O.penalty(y, W, r, periodic=periodic))
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # and a non-Hermitian weight breaks it (the test can fail)
+    A = crandn(L, Ns * r * r, Ns * r * r)
+    lhs = np.vdot(O.penalty(x, A, r, periodic=periodic), y)
+    rhs = np.vdot(x, O.penalty(y, A, r, periodic=periodic))
+    assert abs(lhs - rhs) > 1e-3 * abs(lhs)
+
+
 def test_penalty_interior_equals_periodic_fft_convolution():
     # Away from the border (n in [r-1, N-r]^2) every patch is valid and the
     # penalty is the multichannel correlation with wt_{ii'}[d] = sum_{q-p=d} W[(i',q),(i,p)],
