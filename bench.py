@@ -206,6 +206,7 @@ class Clocks:
 # Only valid for the kernels as captured: a class whose kernel changes is dropped here.
 TRAFFIC_PER_DIRECTION = {
     "eig": (8.665088e6 + 0.532992e6) / 26,      # profiles/k_jacobi_plain_128.md
+    "gram": (27.687680e6 + 78.208256e6) / 26,   # profiles/k_gram_tc_plain_128.md
     "column": (97.608704e6 + 8.169728e6) / 26,  # profiles/k_col_alias_plain_128.md
     "vapply": (38.639616e6 + 0.875264e6) / 26,  # profiles/k_vapply_plain_128.md
 }

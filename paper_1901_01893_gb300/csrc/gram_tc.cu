@@ -375,28 +375,51 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
 
 // G[c][c'] (c <= c') = sum_g (R[c][c'] + R[Cp+c][Cp+c']) + i (R[c][Cp+c'] - R[c'][Cp+c]) in FP64,
 // every entry read from R's upper triangle; G[c'][c] is written as the conjugate, so G is
-// exactly Hermitian.
-__global__ void k_gram_tc_reduce(const float* __restrict__ Rpart, double2* __restrict__ G, int LD, int C, int Cp,
-                                 int nG) {
+// exactly Hermitian.  One CTA (32 x 8 threads) per 32 x 32 tile (c, c') on or above the
+// diagonal: the three terms read along c' are coalesced, and R[c'][Cp+c] is read along c
+// and transposed through shared memory.  The sum over g runs in a fixed order.
+#define GRED_T 32
+__global__ void __launch_bounds__(GRED_T * 8) k_gram_tc_reduce(const float* __restrict__ Rpart,
+                                                               double2* __restrict__ G, int LD, int C, int Cp,
+                                                               int nG) {
+  __shared__ float tr[GRED_T][GRED_T + 1];
+  if (blockIdx.y > blockIdx.x) return;  // tile below the diagonal (uniform per CTA)
   const int R2C = 2 * Cp;
-  const size_t total = (size_t)LD * C * C;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int lf = (int)(e / ((size_t)C * C));
-    const int rem = (int)(e - (size_t)lf * C * C);
-    const int c = rem / C, cc = rem - c * C;
-    if (c > cc) continue;
-    double re = 0.0, im = 0.0;
-    for (int g = 0; g < nG; ++g) {
-      const float* R = Rpart + ((size_t)lf * nG + g) * R2C * R2C;
-      re += (double)R[(size_t)c * R2C + cc] + (double)R[(size_t)(Cp + c) * R2C + Cp + cc];
-      im += (double)R[(size_t)c * R2C + Cp + cc] - (double)R[(size_t)cc * R2C + Cp + c];
+  const int lf = blockIdx.z;
+  const int c0 = blockIdx.y * GRED_T, cc0 = blockIdx.x * GRED_T;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int cc = cc0 + tx;
+  double re[GRED_T / 8], im[GRED_T / 8];
+#pragma unroll
+  for (int k = 0; k < GRED_T / 8; ++k) re[k] = im[k] = 0.0;
+  for (int g = 0; g < nG; ++g) {
+    const float* R = Rpart + ((size_t)lf * nG + g) * R2C * R2C;
+    for (int j = ty; j < GRED_T; j += 8) {  // tr[j][i] = R[cc0 + j][Cp + c0 + i]
+      const int rj = cc0 + j, ci = c0 + tx;
+      tr[j][tx] = (rj < C && ci < C) ? R[(size_t)rj * R2C + Cp + ci] : 0.f;
     }
-    double2* Gl = G + (size_t)lf * C * C;
-    if (c == cc) {
-      Gl[(size_t)c * C + c] = make_double2(re, 0.0);
-    } else {
-      Gl[(size_t)c * C + cc] = make_double2(re, im);
-      Gl[(size_t)cc * C + c] = make_double2(re, -im);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GRED_T / 8; ++k) {
+      const int c = c0 + ty + 8 * k;
+      if (c < C && cc < C && c <= cc) {
+        re[k] += (double)R[(size_t)c * R2C + cc] + (double)R[(size_t)(Cp + c) * R2C + Cp + cc];
+        im[k] += (double)R[(size_t)c * R2C + Cp + cc] - (double)tr[tx][ty + 8 * k];
+      }
+    }
+    __syncthreads();
+  }
+  double2* Gl = G + (size_t)lf * C * C;
+#pragma unroll
+  for (int k = 0; k < GRED_T / 8; ++k) {
+    const int c = c0 + ty + 8 * k;
+    if (c < C && cc < C && c <= cc) {
+      if (c == cc) {
+        Gl[(size_t)c * C + c] = make_double2(re[k], 0.0);
+      } else {
+        Gl[(size_t)c * C + cc] = make_double2(re[k], im[k]);
+        Gl[(size_t)cc * C + c] = make_double2(re[k], -im[k]);
+      }
     }
   }
 }
@@ -466,7 +489,8 @@ smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cu
     k_gram_tc<0><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
                                                                  nG, P->P1, P->periodic);
   SMSM_LAUNCH_CHECK("k_gram_tc");
-  k_gram_tc_reduce<<<512, 256, 0, s>>>(P->Rpart, G, P->LD, P->C, Cp, nG);
+  const int nt = (P->C + GRED_T - 1) / GRED_T;
+  k_gram_tc_reduce<<<dim3(nt, nt, P->LD), dim3(GRED_T, 8), 0, s>>>(P->Rpart, G, P->LD, P->C, Cp, nG);
   SMSM_LAUNCH_CHECK("k_gram_tc_reduce");
   return SMSM_OK;
 }
