@@ -23,8 +23,19 @@ Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
 * sense ..................... pinned (least squares by a dense normal-equation
                               solve at N = 8; exact recovery of a phase-free
                               object)
-* reconstruct ............... pinned (exact recovery with full sampling;
-                              slice-phase equivariance; noiseless recovery)
+* reconstruct ............... pinned (tests/test_oracle_solver_pins.py):
+                              descent of the majorised Eq. 10 cost at fixed
+                              eps; the fixed point is stationary for that
+                              cost (finite differences of its eigenvalue
+                              form); the last normal equations hold;
+                              shot-permutation equivariance; noiseless
+                              recovery (exact at lam = 0, first-order bias
+                              of the penalty at lam > 0); slice- and
+                              global-phase equivariance; each planted
+                              mistake (weight exponent, dropped or halved
+                              penalty, weight never updated) is caught
+* magnitude ................. not used by any parity check (an output
+                              convenience); parity unpinned
 """
 from .smsm_oracle import *  # noqa: F401,F403
 from .smsm_oracle import (DEFAULT_PARAMS, adjoint, caipi_ramp, cg, fft2c, forward, gram,  # noqa: F401

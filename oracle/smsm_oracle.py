@@ -34,7 +34,14 @@ Conventions (readings of the paper, where it is silent or garbled):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+import scipy.fft as _sfft
+
+# the library FFT (pocketfft) run on every host core: the same transform as
+# numpy.fft, threaded over the leading axes
+_WORKERS = os.cpu_count() or 1
 
 # ---------------------------------------------------------------------------
 # Centred unitary DFT (Fig. 1, steps (i) and (iii))
@@ -44,13 +51,13 @@ import numpy as np
 def fft2c(img: np.ndarray) -> np.ndarray:
     """Centred unitary 2D DFT over the last two axes."""
     ax = (-2, -1)
-    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(img, axes=ax), norm="ortho"), axes=ax)
+    return np.fft.fftshift(_sfft.fft2(np.fft.ifftshift(img, axes=ax), norm="ortho", workers=_WORKERS), axes=ax)
 
 
 def ifft2c(ksp: np.ndarray) -> np.ndarray:
     """Inverse of :func:`fft2c` (its adjoint: it is unitary)."""
     ax = (-2, -1)
-    return np.fft.fftshift(np.fft.ifft2(np.fft.ifftshift(ksp, axes=ax), norm="ortho"), axes=ax)
+    return np.fft.fftshift(_sfft.ifft2(np.fft.ifftshift(ksp, axes=ax), norm="ortho", workers=_WORKERS), axes=ax)
 
 
 # ---------------------------------------------------------------------------
@@ -66,9 +73,14 @@ def caipi_ramp(L: int, N: int, Ldiv: int | None = None) -> np.ndarray:
     return np.exp(-2j * np.pi * l * (n - N / 2) / Ldiv)
 
 
-def shot_lines(Ns: int, N: int, i: int) -> np.ndarray:
-    """Phase-encode lines kept by shot i: n = m*Ns + i, m = 0..N/Ns-1 (Eq. 2)."""
-    return np.arange(N // Ns) * Ns + i
+def shot_lines(Ns: int, N: int, i: int, offsets=None) -> np.ndarray:
+    """Phase-encode lines kept by shot i: n = m*Ns + i, m = 0..N/Ns-1 (Eq. 2).
+
+    ``offsets`` (a permutation of 0..Ns-1, default the identity) lets shot i
+    acquire the interleave n = m*Ns + offsets[i] instead: the same sampling
+    with the shots relabelled, which the shot-permutation pin uses."""
+    o = i if offsets is None else int(offsets[i])
+    return np.arange(N // Ns) * Ns + o
 
 
 # ---------------------------------------------------------------------------
@@ -77,7 +89,7 @@ def shot_lines(Ns: int, N: int, i: int) -> np.ndarray:
 
 
 def forward(x: np.ndarray, sens: np.ndarray, Ns: int | None = None, Ldiv: int | None = None,
-            phase: np.ndarray | None = None, full: bool = False) -> np.ndarray:
+            phase: np.ndarray | None = None, full: bool = False, offsets=None) -> np.ndarray:
     """y = A(x), Fig. 1 steps (i)-(v).
 
     x     : [L][Ns][N][N] per-shot centred k-space (the unknown of Eq. 10), or
@@ -85,6 +97,7 @@ def forward(x: np.ndarray, sens: np.ndarray, Ns: int | None = None, Ldiv: int | 
     sens  : [L][Nc][N][N] coil sensitivities (image domain).
     phase : optional [L][Ns][N][N] image-domain shot phase phi_{l,i} (Eq. 4).
     full  : keep every line for every shot (used only by the exact-recovery pin).
+    offsets : line interleave of each shot (see :func:`shot_lines`).
     returns y : [Ns][Nc][N/Ns][N] (or [Ns][Nc][N][N] when ``full``).
     """
     L, S1, N, _ = x.shape
@@ -104,20 +117,20 @@ def forward(x: np.ndarray, sens: np.ndarray, Ns: int | None = None, Ldiv: int | 
         coil = sens * img[:, None]                       # (ii) [L][Nc][N][N]
         K = fft2c(coil)                                  # (iii)
         Ksum = np.sum(theta[:, None, :, None] * K, axis=0)  # (iv) CAIPI phase + slice sum
-        lines = np.arange(N) if full else shot_lines(Ns, N, i)
+        lines = np.arange(N) if full else shot_lines(Ns, N, i, offsets)
         y[i] = Ksum[:, lines, :]                         # (v) shot mask
     return y
 
 
 def adjoint(y: np.ndarray, sens: np.ndarray, L: int, Ldiv: int | None = None,
-            phase: np.ndarray | None = None, full: bool = False) -> np.ndarray:
+            phase: np.ndarray | None = None, full: bool = False, offsets=None) -> np.ndarray:
     """x = A^H(y): the transpose of each step of :func:`forward`, in reverse order."""
     Ns, Nc, rows, N = y.shape
     theta = caipi_ramp(L, N, Ldiv)
     out = np.zeros((L, 1 if phase is not None else Ns, N, N), dtype=np.complex128)
     for i in range(Ns):
         Kfull = np.zeros((Nc, N, N), dtype=np.complex128)
-        lines = np.arange(N) if full else shot_lines(Ns, N, i)
+        lines = np.arange(N) if full else shot_lines(Ns, N, i, offsets)
         Kfull[:, lines, :] = y[i]                                 # (v)^H
         K = np.conj(theta)[:, None, :, None] * Kfull[None]        # (iv)^H [L][Nc][N][N]
         coil = ifft2c(K)                                          # (iii)^H
@@ -129,10 +142,10 @@ def adjoint(y: np.ndarray, sens: np.ndarray, L: int, Ldiv: int | None = None,
     return fft2c(out)                                             # (i)^H
 
 
-def normal(x: np.ndarray, sens: np.ndarray, Ldiv: int | None = None) -> np.ndarray:
+def normal(x: np.ndarray, sens: np.ndarray, Ldiv: int | None = None, offsets=None) -> np.ndarray:
     """A^H A x for the per-shot unknown."""
     L, Ns = x.shape[:2]
-    return adjoint(forward(x, sens, Ns=Ns, Ldiv=Ldiv), sens, L, Ldiv=Ldiv)
+    return adjoint(forward(x, sens, Ns=Ns, Ldiv=Ldiv, offsets=offsets), sens, L, Ldiv=Ldiv, offsets=offsets)
 
 
 # ---------------------------------------------------------------------------
@@ -259,7 +272,7 @@ DEFAULT_PARAMS = dict(lam=1e-2, eps0_rel=1e-2, eta=1.5, eps_min_rel=1e-4, K=10, 
 
 def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = None,
                 x0: np.ndarray | None = None, Ldiv: int | None = None,
-                report: dict | None = None) -> np.ndarray:
+                report: dict | None = None, offsets=None) -> np.ndarray:
     """SMS-MUSSELS joint recovery of the slice-unfolded per-shot k-space.
 
     Outer iteration k = 1..K: G_l = H_l^H H_l of the current x; eigen-
@@ -267,16 +280,22 @@ def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = N
     (A^H A + lam P_W) x = A^H y from the current x.
     eps_1 = eps0_rel * max_l s_max(G_l) at k = 1, eps_k = max(eps_{k-1}/eta,
     eps_min_rel * eps_1).
+
+    ``report`` (a dict, optional) receives ``hist``: per outer iteration its
+    eps and the CG residual norms; with ``report["keep_iterates"]`` true also
+    the weight W used and the iterate x after that iteration's CG steps.
+    ``offsets``: line interleave of each shot (see :func:`shot_lines`).
     """
     p = dict(DEFAULT_PARAMS)
     if params:
         p.update(params)
     Ns = y.shape[0]
     L = sens.shape[0]
-    b = adjoint(y, sens, L, Ldiv=Ldiv)
+    b = adjoint(y, sens, L, Ldiv=Ldiv, offsets=offsets)
     x = b.copy() if x0 is None else np.array(x0, dtype=np.complex128)
     eps = eps_min = None
     hist = []
+    keep = bool(report is not None and report.get("keep_iterates"))
     per = bool(p["periodic"])
     for k in range(p["K"]):
         G = gram(x, r, per)
@@ -293,10 +312,10 @@ def reconstruct(y: np.ndarray, sens: np.ndarray, r: int, params: dict | None = N
         lam = p["lam"]
 
         def apply_N(v, W=W):
-            return normal(v, sens, Ldiv) + lam * penalty(v, W, r, per)
+            return normal(v, sens, Ldiv, offsets) + lam * penalty(v, W, r, per)
 
         x, h = cg(apply_N, b, x, p["J"])
-        hist.append(dict(eps=eps, rr=h))
+        hist.append(dict(eps=eps, rr=h, W=W, x=x.copy()) if keep else dict(eps=eps, rr=h))
     if report is not None:
         report["hist"] = hist
     return x
