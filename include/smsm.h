@@ -48,7 +48,10 @@ typedef enum {
   SMSM_ERR_DIVERGED = 4,  /* a CG scalar became NaN/Inf (reported via smsm_report) */
   SMSM_ERR_NOT_PD = 5,    /* <p, N p> <= 0 in CG: system not positive definite */
   SMSM_ERR_TIMEOUT = 6,   /* reserved: a bounded device wait gave up */
-  SMSM_ERR_STATE = 7      /* call out of order, e.g. no coil maps set yet */
+  SMSM_ERR_STATE = 7,     /* call out of order, e.g. no coil maps set yet */
+  SMSM_ERR_EIG_UNCONVERGED = 8 /* the Jacobi eigen step hit smsm_params.max_sweeps with a
+                                  rotation still pending (reported via smsm_report; the
+                                  solve ran on with the last rotations) */
 } smsm_status;
 
 typedef enum { SMSM_MODE_IRLS = 0, SMSM_MODE_NULLSPACE = 1 } smsm_mode;
@@ -74,9 +77,11 @@ typedef struct {
 /*
  * Precision of the Hankel Gram, which runs on the tensor cores when C <= 144
  * (larger C: FP32 FMA; the BF16 split form needs C <= 144):
- *   FP32: every value split as x = hi + lo with hi a TF32 value, three TF32
- *         products hi*hi + hi*lo + lo*hi, FP32 accumulation (FP32-accurate);
- *   BF16_SPLIT: the same with BF16 hi and lo (~2^-16 relative per product).
+ *   FP32: every FP32 value split exactly into three BF16 pieces b1 + b2 + b3,
+ *         six BF16 products b_i b_j' (i + j <= 4), FP32 accumulation: every
+ *         product as accurate as an FP32 multiply;
+ *   BF16_SPLIT: two pieces hi = bf16(x), lo = bf16(x - hi), three products
+ *         hi hi' + hi lo' + lo hi' (~2^-16 relative per product).
  */
 typedef enum { SMSM_PRECISION_FP32 = 0, SMSM_PRECISION_BF16_SPLIT = 1 } smsm_precision;
 
@@ -116,7 +121,9 @@ typedef struct {
   int mode;           /* smsm_mode */
   int rank;           /* NULLSPACE rank, 0 < rank < C */
   int warm;           /* 1: x holds the starting point on entry; 0: start from A^H y */
-  int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 15 */
+  int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 30 (the most the rotation
+                         log holds); reaching it with rotations pending sets
+                         SMSM_ERR_EIG_UNCONVERGED */
   int timing;         /* bitmask of (1 << smsm_stage): bracket those launches with CUDA
                          events inside the solve and report their device time */
   int eig_cold;       /* 1: restart the eigensolver from scratch every outer iteration
@@ -293,6 +300,51 @@ smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, i
  */
 smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, int n, int filter,
                                      void* stream);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper, which starts its iteration from the
+ * data alone).  A complex CNN maps the aliased, zero-filled image of every
+ * (slice, shot), a = F^-1(A^H y) ([n][B][H][W] complex64, B = L*Ns), to a
+ * starting image x0 = a + f(a): f is `layers` complex 3x3 convolutions
+ * (cross-correlation, zero padding) with channels B -> width -> ... -> B and
+ * CReLU (ReLU of the real and of the imaginary part) between them.  The start
+ * seeds the k-space of the IRLS solve of Eq. 10 and so its first Gram and
+ * annihilating filters (Eq. 9).  Weights: FP32 master copies, every product
+ * taken with the weight rounded to BF16, FP32 activations and accumulation.
+ * Parameters are one complex64 vector: for each layer k, W_k [Cout][Cin][3][3]
+ * then b_k [Cout].  Loss of a sample ||x0 - t||^2 / ||t||^2, averaged over the
+ * batch; gradients are given as dL/dRe + i dL/dIm.  All pointers are device
+ * pointers, 16-byte aligned, owned by the caller; calls are asynchronous on
+ * `stream` except where a host `loss` is requested (then they synchronise).
+ * ------------------------------------------------------------------------ */
+typedef struct smsm_cnn_s* smsm_cnn_t;
+
+/* Create a network for images of height x wdt with `channels` = B input and output
+ * channels and `width` hidden ones; buffers for batches up to max_batch are held
+ * (activations of every layer, for training).  Parameters start at zero: set them. */
+smsm_status smsm_cnn_create(smsm_cnn_t* out, int channels, int width, int layers, int height, int wdt,
+                            int max_batch);
+smsm_status smsm_cnn_destroy(smsm_cnn_t cnn);
+/* Number of complex parameters. */
+size_t smsm_cnn_param_count(smsm_cnn_t cnn);
+/* Copy params [count] complex64 in (also clears the optimiser's moments), or out. */
+smsm_status smsm_cnn_set_params(smsm_cnn_t cnn, const void* params, void* stream);
+smsm_status smsm_cnn_get_params(smsm_cnn_t cnn, void* params, void* stream);
+/* x0 = a + f(a) for n samples (a and x0 distinct). */
+smsm_status smsm_cnn_forward(smsm_cnn_t cnn, const void* a, void* x0, int n, void* stream);
+/* Loss of the n samples (a, target t) and its gradient grad [count]; `loss` (host,
+ * nullable) receives the mean loss after a synchronisation. */
+smsm_status smsm_cnn_gradients(smsm_cnn_t cnn, const void* a, const void* t, int n, void* grad, double* loss,
+                               void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the gradient of
+ * the batch's loss. */
+smsm_status smsm_cnn_train_step(smsm_cnn_t cnn, const void* a, const void* t, int n, float lr, double* loss,
+                                void* stream);
+/* The learned starting point of every problem of `plan`: x = F(cnn(F^-1(A^H y))),
+ * y [D][Ns][Nc][N/Ns][N], x [D][L][Ns][N][N] (the layouts of smsm_reconstruct).
+ * Needs cnn channels = L*Ns, an N x N image and max_batch >= D.  Pass x to
+ * smsm_reconstruct with params->warm = 1. */
+smsm_status smsm_learned_start(smsm_plan_t plan, smsm_cnn_t cnn, const void* y, void* x, void* stream);
 
 /*
  * Synchronise `stream` and report the plan's device error flag: SMSM_OK, or

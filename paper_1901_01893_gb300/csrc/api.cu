@@ -36,7 +36,7 @@ extern "C" void smsm_default_params(smsm_params* p) {
   p->mode = SMSM_MODE_IRLS;
   p->rank = 0;
   p->warm = 0;
-  p->max_sweeps = 15;
+  p->max_sweeps = SMSM_MAX_SWEEPS;
 }
 
 // ---------------------------------------------------------------------------
@@ -94,7 +94,7 @@ static void free_plan(smsm_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->twN,  P->twM,  P->tw_shot, P->cph,  P->Etab,  P->sensT, P->hA,   P->hB,
                   P->yh,   P->phaseT, P->xs,    P->bv,   P->rv,    P->pv,    P->qv,   P->ybuf,
-                  P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2,
+                  P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2, P->Gw3,
                   P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep,
                   P->Rpart, P->devflag, P->acorr, P->ash};
   for (void* p : ptrs)
@@ -233,6 +233,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(Wf, LD * C * C);
   A(Gw, LD * C * C);
   A(Gw2, LD * C * C);
+  A(Gw3, LD * C * C);
   A(wper, LD * shots * shots * R2 * R2);
   A(wcls, LD * R2 * R2 * shots * shots * R2 * R2);
   A(multT, LD * mult_planes(shots) * NN);
@@ -582,4 +583,24 @@ extern "C" smsm_status smsm_sense(smsm_plan_t plan, const void* y, const void* p
     return SMSM_ERR_ARG;
   }
   return solver_sense(plan, y, phase, x, cg_iters, report, S(stream));
+}
+
+// x = F(cnn(F^-1(A^H y))) for the plan's batch; the plan's work vectors hold a and x0
+extern "C" smsm_status smsm_learned_start(smsm_plan_t plan, smsm_cnn_t cnn, const void* y, void* x, void* stream) {
+  CHECK_PLAN("smsm_learned_start");
+  CHECK_PTR("smsm_learned_start", y);
+  CHECK_PTR("smsm_learned_start", x);
+  int B = 0, H = 0, W = 0, maxn = 0;
+  if (!cnn || cnn_shape(cnn, &B, &H, &W, &maxn) || B != plan->L * plan->Ns || H != plan->N || W != plan->N ||
+      maxn < plan->D) {
+    smsm_set_error("smsm_learned_start: the network must take L*Ns = %d channels of %d x %d images and batches "
+                   "of %d", plan->L * plan->Ns, plan->N, plan->N, plan->D);
+    return SMSM_ERR_ARG;
+  }
+  smsm_status st;
+  const int count = plan->D * plan->L * plan->Ns;
+  if ((st = smsm_adjoint(plan, y, nullptr, x, stream))) return st;
+  if ((st = smsm_fft2c(plan, x, plan->bv, count, 1, stream))) return st;
+  if ((st = smsm_cnn_forward(cnn, plan->bv, plan->pv, plan->D, stream))) return st;
+  return smsm_fft2c(plan, plan->pv, x, count, 0, stream);
 }

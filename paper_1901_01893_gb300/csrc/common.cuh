@@ -133,7 +133,8 @@ struct smsm_plan_s {
   float4* rotlog;    // [L][SMSM_MAX_SWEEPS][Cp-1][Cp/2]
   int* sweeps;       // [L]
   float2 *V, *Wf;    // [LD][C][C]
-  float2 *Gw, *Gw2;  // [LD][C][C] warm-start congruence V^H G V (and its half product)
+  float2 *Gw, *Gw2, *Gw3;  // [LD][C][C] warm-start congruence V^H G V: G V as hi/lo FP32 pairs
+                           // (Gw, Gw3), then the result rounded to FP32 (Gw2)
   float2* wper;      // [L][Ns][Ns][R2*R2]
   float2* wcls;      // [LD][R2*R2 classes][Ns (i')][R2*R2 taps][Ns (i)] border correction taps
   float2* multT;     // [L][Ns(Ns+1)/2][N(x)][N(y)]: upper triangle of the Hermitian shot coupling
@@ -282,6 +283,8 @@ smsm_status operators_init_attrs();
 size_t smsm_col_smem_bytes(const smsm_plan_s* P);
 int band_blocks(const smsm_plan_s* P);
 smsm_status band_init_attrs(const smsm_plan_s* P);
+// cnn.cu
+smsm_status cnn_shape(const smsm_cnn_s* c, int* B, int* H, int* W, int* maxn);
 // solver.cu
 int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,

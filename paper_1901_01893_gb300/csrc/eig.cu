@@ -13,10 +13,19 @@
 // the rows of V (independent rows, spread over many CTAs), so V never has to
 // share the CTA's shared memory with G.
 //
-// Precision: FP32 storage and rotations.  The Gram itself is only
-// FP32-accurate (its inputs are FP32), and a Jacobi sweep is backward stable
-// to u*||G||, so an FP64 eigensolver would not make W more accurate -- while
-// FP64 on this part runs at about 1/60 of the FP32 rate.
+// Precision: the Gram arrives in FP64 and is rounded once to FP32 on load; rotations
+// are FP32.  What decides the accuracy of W is not the arithmetic width of the
+// rotations but two things around them:
+//  * no rotation is skipped because it is small next to the largest eigenvalue:
+//    W = (G + eps I)^(-1/2) is largest on the smallest eigenvalues (down to eps_min),
+//    so off-diagonal entries far below s_max still move W there.  The only absolute
+//    floor is tied to eps_min (a thousandth of it), where W no longer changes;
+//  * V stays orthonormal: the rotations of one eigen step (and the warm starts from
+//    the previous V) would otherwise add their rounding to V's orthogonality from
+//    one outer iteration to the next.  After every eigen step V is re-orthonormalised
+//    by a Newton-Schulz step V <- V (3I - V^H V)/2, which squares the error.
+// A sweep cap that ends the Jacobi with rotations still pending is reported
+// (SMSM_ERR_EIG_UNCONVERGED in the solve's status) instead of passing silently.
 #include <math.h>
 
 #include "common.cuh"
@@ -77,7 +86,7 @@ __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, 
 __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, const float2* __restrict__ Gw,
                                                  float* __restrict__ eig, float4* __restrict__ rlog,
                                                  int* __restrict__ sweeps_out, int C, int Cp, int max_sweeps,
-                                                 float tol) {
+                                                 float tol, float floor_rel, SolverState* st, int L) {
   extern __shared__ float2 g[];
   const int ld = Cp + 1;
   const int half = Cp / 2;
@@ -109,8 +118,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   __syncthreads();
   if (tid < Cp) atomicMax(reinterpret_cast<int*>(&dmax), __float_as_int(fmaxf(g[tid * ld + tid].x, 0.f)));
   __syncthreads();
-  // rotations below this absolute size only churn rounding noise
-  const float floor_abs = 1e-7f * dmax;
+  // absolute floor of the rotation test: a thousandth of eps_min (given relative to the
+  // largest diagonal entry), far below every eigenvalue that W resolves
+  const float floor_abs = floor_rel * dmax;
   // this thread's blocks of the folded triangle, the same in every round
   int kb1[JAC_BLK], kb2[JAC_BLK];
 #pragma unroll
@@ -123,6 +133,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
     }
   }
   int sw = 0;
+  int pending = 1;  // the last sweep (or the direct test after it) found a pair to rotate
   for (; sw < max_sweeps; ++sw) {
     int rotated = 0;  // this thread set a non-identity rotation during the sweep
     for (int round = 0; round < Cp - 1; ++round) {
@@ -196,7 +207,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
       }
       __syncthreads();
     }
-    if (!__syncthreads_or(rotated)) break;
+    if (!__syncthreads_or(rotated)) {
+      pending = 0;
+      break;
+    }
     // A sweep that sets no rotation changes nothing, and it sets none exactly when no
     // pair passes the rotation test on the current matrix: test every pair directly
     // (same arithmetic as the rotation step) instead of running that sweep.
@@ -210,9 +224,13 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
     }
     if (!__syncthreads_or(need)) {
       ++sw;
+      pending = 0;
       break;
     }
   }
+  // sweep cap reached with a pair still above the rotation test: report it (unless an
+  // earlier error of this problem is already recorded)
+  if (pending && tid == 0 && st) atomicCAS(&st[l / L].status, 0, (int)SMSM_ERR_EIG_UNCONVERGED);
   for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
 }
@@ -319,11 +337,87 @@ __global__ void __launch_bounds__(32 * VA_WARPS) k_vapply(const float4* __restri
   }
 }
 
-// Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
-// step 0: T = G V (G in FP64, rounded on load); step 1: Gw = V^H T.
+// Warm start: Gw = V^H G V, the previous eigenvectors' Rayleigh-Ritz projection of the new
+// Gram, formed in double-FP32 arithmetic so that its small entries -- the block of the
+// smallest eigenvalues, where W = (G + eps I)^(-1/2) is largest -- are accurate relative
+// to themselves, not only to s_max: every product is split exactly (a * b = p + e with
+// e = fma(a, b, -p)) and summed into a (hi, lo) pair with an error-free two-sum.
+// step 0: T = G V (G in FP64 as hi + lo FP32, V in FP32) -> (Thi, Tlo);
+// step 1: Gw = V^H (Thi + Tlo), rounded once to FP32.
+struct Df {  // hi + lo, |lo| <= ulp(hi)/2 after each add
+  float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(Df& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (p - bb);
+  s.hi = t;
+  s.lo += err + e;
+}
 __global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ G, const float2* __restrict__ V,
-                                                    const float2* __restrict__ Tin, float2* __restrict__ out, int C,
+                                                    const float2* __restrict__ Thi, const float2* __restrict__ Tlo,
+                                                    float2* __restrict__ out, float2* __restrict__ out_lo, int C,
                                                     int step) {
+  __shared__ float2 Ah[CG_T][CG_T + 1], Al[CG_T][CG_T + 1];
+  __shared__ float2 Bh[CG_T][CG_T + 1], Bl[CG_T][CG_T + 1];
+  const int l = blockIdx.z;
+  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
+  const int a = blockIdx.y * CG_T + ty, b = blockIdx.x * CG_T + tx;
+  const size_t off = (size_t)l * C * C;
+  Df re{0.f, 0.f}, im{0.f, 0.f};
+  for (int k0 = 0; k0 < C; k0 += CG_T) {
+    const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
+    const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
+    float2 ah = cmk(0.f, 0.f), al = cmk(0.f, 0.f), bh = cmk(0.f, 0.f), bl = cmk(0.f, 0.f);
+    if (ar < C && ak < C) {
+      if (step == 0) {
+        const double2 gv = G[off + (size_t)ar * C + ak];
+        ah = cmk((float)gv.x, (float)gv.y);
+        al = cmk((float)(gv.x - (double)ah.x), (float)(gv.y - (double)ah.y));
+      } else {
+        ah = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
+      }
+    }
+    if (bk < C && bc < C) {
+      if (step == 0) {
+        bh = V[off + (size_t)bk * C + bc];
+      } else {
+        bh = Thi[off + (size_t)bk * C + bc];
+        bl = Tlo[off + (size_t)bk * C + bc];
+      }
+    }
+    Ah[ty][tx] = ah;
+    Al[ty][tx] = al;
+    Bh[ty][tx] = bh;
+    Bl[ty][tx] = bl;
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < CG_T; ++k) {
+      const float2 x = Ah[ty][k], y = Bh[k][tx];
+      df_add_prod(re, x.x, y.x);
+      df_add_prod(re, -x.y, y.y);
+      df_add_prod(im, x.x, y.y);
+      df_add_prod(im, x.y, y.x);
+      // the low parts: products of small terms, rounded once
+      const float2 xl = Al[ty][k], yl = Bl[k][tx];
+      re.lo = fmaf(xl.x, y.x, fmaf(-xl.y, y.y, fmaf(x.x, yl.x, fmaf(-x.y, yl.y, re.lo))));
+      im.lo = fmaf(xl.x, y.y, fmaf(xl.y, y.x, fmaf(x.x, yl.y, fmaf(x.y, yl.x, im.lo))));
+    }
+    __syncthreads();
+  }
+  if (a < C && b < C) {
+    const float rh = re.hi + re.lo, ih = im.hi + im.lo;
+    out[off + (size_t)a * C + b] = cmk(rh, ih);
+    if (step == 0) out_lo[off + (size_t)a * C + b] = cmk((re.hi - rh) + re.lo, (im.hi - ih) + im.lo);
+  }
+}
+
+// Newton-Schulz re-orthonormalisation of V (one step squares the orthogonality error):
+// step 0: M = V^H V;  step 1: out = V (3I - M) / 2.  16 x 16 output tiles, FP32.
+__global__ void __launch_bounds__(256) k_ns(const float2* __restrict__ V, const float2* __restrict__ M,
+                                            float2* __restrict__ out, int C, int step) {
   __shared__ float2 As[CG_T][CG_T + 1];
   __shared__ float2 Bs[CG_T][CG_T + 1];
   const int l = blockIdx.z;
@@ -332,19 +426,18 @@ __global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ 
   const size_t off = (size_t)l * C * C;
   float2 acc = cmk(0.f, 0.f);
   for (int k0 = 0; k0 < C; k0 += CG_T) {
-    // A tile: rows a-block, cols k;  B tile: rows k, cols b-block
     const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
     const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
     float2 av = cmk(0.f, 0.f), bv = cmk(0.f, 0.f);
-    if (ar < C && ak < C) {
+    if (ar < C && ak < C) av = step == 0 ? conjf2(V[off + (size_t)ak * C + ar]) : V[off + (size_t)ar * C + ak];
+    if (bk < C && bc < C) {
       if (step == 0) {
-        const double2 gv = G[off + (size_t)ar * C + ak];
-        av = cmk((float)gv.x, (float)gv.y);
+        bv = V[off + (size_t)bk * C + bc];
       } else {
-        av = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
+        const float2 m = M[off + (size_t)bk * C + bc];
+        bv = cmk(((bk == bc ? 3.f : 0.f) - m.x) * 0.5f, -0.5f * m.y);
       }
     }
-    if (bk < C && bc < C) bv = step == 0 ? V[off + (size_t)bk * C + bc] : Tin[off + (size_t)bk * C + bc];
     As[ty][tx] = av;
     Bs[ty][tx] = bv;
     __syncthreads();
@@ -460,20 +553,24 @@ size_t eig_jacobi_smem(int Cp) { return jacobi_smem(Cp); }
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T) {
   const int Cp = P->Cp, C = P->C;
-  int msw = prm->max_sweeps > 0 ? prm->max_sweeps : 15;
+  int msw = prm->max_sweeps > 0 ? prm->max_sweeps : SMSM_MAX_SWEEPS;
   if (msw > SMSM_MAX_SWEEPS) msw = SMSM_MAX_SWEEPS;
   // warm start from the previous outer iteration's eigenvectors (same solve)
   const int warm = (outer > 0 && !prm->eig_cold) ? 1 : 0;
   if (T) T->begin(SMSM_STAGE_EIG);
   if (warm) {
     dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, nullptr, P->Gw, P->Gw3, C, 0);
     SMSM_LAUNCH_CHECK("k_congruence");
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw2, C, 1);
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw3, P->Gw2, nullptr, C, 1);
     SMSM_LAUNCH_CHECK("k_congruence");
   }
+  // rotation floor: a thousandth of eps_min relative to the largest diagonal entry (IRLS;
+  // eps_min = eps_min_rel * eps0_rel * s_max), 1e-9 of it for the fixed-rank projector
+  double frel = prm->mode == SMSM_MODE_NULLSPACE ? 1e-9 : 1e-3 * prm->eps0_rel * prm->eps_min_rel;
+  if (!(frel > 0.0)) frel = 1e-9;
   k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->rotlog, P->sweeps, C, Cp,
-                                                 msw, 1e-6f);
+                                                 msw, 1e-6f, (float)frel, P->st, P->L);
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
@@ -481,6 +578,14 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   k_vapply<<<gv, 32 * VA_WARPS, (size_t)VA_WARPS * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
                                                                               warm);
   SMSM_LAUNCH_CHECK("k_vapply");
+  {
+    dim3 gn((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
+    k_ns<<<gn, CG_T * CG_T, 0, s>>>(P->V, nullptr, P->Gw, C, 0);
+    SMSM_LAUNCH_CHECK("k_ns");
+    k_ns<<<gn, CG_T * CG_T, 0, s>>>(P->V, P->Gw, P->Gw2, C, 1);
+    SMSM_LAUNCH_CHECK("k_ns");
+    SMSM_CUDA_TRY(cudaMemcpyAsync(P->V, P->Gw2, sizeof(float2) * (size_t)P->LD * C * C, cudaMemcpyDeviceToDevice, s));
+  }
   if (T) T->end(SMSM_STAGE_VAPPLY);
   if (T) T->begin(SMSM_STAGE_WEIGHTS);
   k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, C, Cp, outer, prm->eps0_rel, prm->eta,

@@ -15,20 +15,26 @@
 //   * thread 0 brings the window of patch row ky -- image rows ky..ky+r-1 of
 //     every shot -- into shared memory with TMA bulk copies (two windows in
 //     flight, completion counted on an mbarrier);
-//   * the producer warps build each chunk of KCH patches (32 bytes along K) from the
-//     window (implicit im2col), split every value into hi + lo and write X^T
-//     (all 2Cp rows, hi and lo) into a 3-stage ring in the canonical K-major
+//   * the producer warps build each chunk of KCH patches from the window
+//     (implicit im2col), split every value into BF16 pieces and write X^T (all
+//     2Cp rows, every piece) into a ring of stages in the canonical K-major
 //     layout;
-//   * one thread of the last warp issues  D_t += Xh_t Xh_c^T + Xh_t Xl_c^T +
-//     Xl_t Xh_c^T  for every tile t (A and B are row windows of the same staged
-//     X^T) and commits each stage back to its producers;
+//   * one thread of the last warp issues the piece products D_t += X1_t X1_c^T +
+//     ... for every tile t (A and B are row windows of the same staged X^T) and
+//     commits each stage back to its producers;
 //   * four warps drain the TMEM accumulator every GTC_EPOCH chunks into the
 //     CTA's FP32 partial in global memory (each thread owns one row per tile and adds
 //     with fire-and-forget reductions), which bounds the error
 //     that the tensor core's FP32 accumulation gathers over many chunks.
-//   precision 0: TF32 split (hi = x with the low 13 mantissa bits cleared,
-//                lo = x - hi): products accurate to ~2^-21, like FP32 FMA.
-//   precision 1: BF16 split (hi = bf16(x), lo = bf16(x - hi)): ~2^-16.
+//   PREC 2 (the FP32 form): every FP32 value split into three BF16 pieces,
+//                b1 = bf16(x), b2 = bf16(x - b1), b3 = bf16(x - b1 - b2), which hold
+//                its 24 significant bits exactly; six products b_i b_j' with
+//                i + j <= 4 (the dropped ones are below 2^-24 of the product), so
+//                every product is as accurate as an FP32 multiply;
+//   PREC 1 (the reduced-precision form): two pieces hi = bf16(x), lo = bf16(x - hi)
+//                and three products hi hi' + hi lo' + lo hi' (~2^-16 per product).
+//   A third form, a TF32 hi + lo split with three products, was measured 9x less
+//   accurate than FP32 FMA (2^-22 of every operand is lost) and is not kept.
 // Every wait on an mbarrier is bounded; on a timeout the kernel raises the
 // plan's device error flag, lets its in-flight bulk copies and MMAs finish
 // (bounded waits), frees TMEM and returns.
@@ -41,7 +47,6 @@
 
 #define GTC_PROD_WARPS 6                               // im2col producers
 #define GTC_THREADS (32 * (GTC_PROD_WARPS + 4 + 1))     // + 4 drain warps + 1 MMA warp
-#define GTC_KSTEP 2                                    // MMA k-steps (32 bytes of K each) per staged chunk
 #define GTC_EPOCH 16                                   // chunks accumulated in TMEM before a drain
 #define GTC_MAXITER (1L << 22)
 
@@ -65,22 +70,28 @@ struct GtcLayout {
   int rows_alloc;    // 128 * number of row tiles
   int wp;            // window row pitch (complex elements): N + 8 (+16), shifts consecutive rows by 8 banks
   int ext;           // periodic: the first ext (even, >= r-1) elements of a row repeated after it
-  size_t arr_bytes;  // one of hi / lo of one staged chunk: rows_alloc x (32 GTC_KSTEP) bytes
+  int planes;        // operand pieces staged per chunk (2 or 3)
+  size_t arr_bytes;  // one piece of one staged chunk: rows_alloc x (32 * k-steps) bytes
   size_t win_elems;  // one window: Ns*r rows of wp elements
   int nst;           // ring stages (3, or 2 when three do not fit)
   size_t total;
 };
 
-__host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp, int periodic) {
+// Operand pieces and MMA k-steps (32 bytes of K each) per staged chunk of each form.
+__host__ __device__ constexpr int gtc_planes(int prec) { return prec == 2 ? 3 : 2; }
+__host__ __device__ constexpr int gtc_ksteps(int prec) { return prec == 2 ? 1 : 2; }
+
+__host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp, int periodic, int prec) {
   GtcLayout L;
   L.rows_alloc = 128 * ((2 * Cp + 127) / 128);
   L.ext = periodic ? ((r - 1 + 1) & ~1) : 0;
   L.wp = N + (L.ext > 8 ? 24 : 8);
-  L.arr_bytes = (size_t)L.rows_alloc * 32 * GTC_KSTEP;
+  L.planes = gtc_planes(prec);
+  L.arr_bytes = (size_t)L.rows_alloc * 32 * gtc_ksteps(prec);
   L.win_elems = (size_t)Ns * r * L.wp;
   const size_t win = 2 * L.win_elems * 8;
-  L.nst = (2 * 3 * L.arr_bytes + win <= (size_t)224 * 1024) ? 3 : 2;
-  L.total = 2 * L.nst * L.arr_bytes + win;
+  L.nst = (L.planes * 3 * L.arr_bytes + win <= (size_t)224 * 1024) ? 3 : 2;
+  L.total = L.planes * L.nst * L.arr_bytes + win;
   return L;
 }
 
@@ -96,16 +107,18 @@ __host__ __device__ inline int gtc_tmem_cols(int R2C) {
 }
 
 // This CTA: every row tile of R, patch rows ky in [ky0, ky1) (block g of nG), matrix lf.
-// A chunk is KCH = 32 GTC_KSTEP / ESZ consecutive patches of one patch row (the row's
+// A chunk is KCH = 32 KSTEP / ESZ consecutive patches of one patch row (the row's
 // tail zero-padded).  Producer unit = one 16-byte core-matrix row: column c of X (its
 // Re and Im rows of X^T), EPC consecutive patches.
 template <int PREC>
 __global__ void __launch_bounds__(GTC_THREADS, 1)
     k_gram_tc(const float2* __restrict__ x, float* __restrict__ Rpart, int* __restrict__ errflag, int Ns, int N,
               int r, int C, int Cp, int nG, int P1, int periodic) {
-  constexpr int ESZ = PREC == 0 ? 4 : 2;         // bytes per operand element
+  constexpr int ESZ = 2;                         // bytes per operand element (BF16)
   constexpr int EPC = 16 / ESZ;                  // elements per 16-byte core-matrix row
-  constexpr int KQ = 2 * GTC_KSTEP;              // core matrices along K per chunk
+  constexpr int KSTEP = gtc_ksteps(PREC);        // MMA k-steps per staged chunk
+  constexpr int NPL = gtc_planes(PREC);          // operand pieces per chunk
+  constexpr int KQ = 2 * KSTEP;                  // core matrices along K per chunk
   constexpr int KCH = KQ * EPC;                  // patches per chunk
   constexpr uint32_t LBO = 128;                  // next core matrix along K
   constexpr uint32_t SBO = 128 * KQ;             // next 8-row group
@@ -118,12 +131,12 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const int g = blockIdx.x, lf = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R2C = 2 * Cp;
-  const GtcLayout Lo = gtc_layout(Ns, N, r, Cp, periodic);
+  const GtcLayout Lo = gtc_layout(Ns, N, r, Cp, periodic, PREC);
   const int ntile = Lo.rows_alloc / 128;
   const int NST = Lo.nst;
   const size_t arr_bytes = Lo.arr_bytes;
   const int WP = Lo.wp;
-  float2* win = reinterpret_cast<float2*>(gsm + 2 * NST * arr_bytes);  // [2][Ns*r][WP]
+  float2* win = reinterpret_cast<float2*>(gsm + NPL * NST * arr_bytes);  // [2][Ns*r][WP]
   const int ky0 = (int)((long)g * P1 / nG), ky1 = (int)((long)(g + 1) * P1 / nG);
   const int nchx = (P1 + KCH - 1) / KCH;
   const int nit = (ky1 - ky0) * nchx;
@@ -134,7 +147,7 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   const uint32_t win_bytes = (uint32_t)((size_t)Ns * r * (N + Lo.ext) * sizeof(float2));
   const int tmem_cols = gtc_tmem_cols(R2C);
 
-  for (size_t e = tid; e < 2 * NST * arr_bytes / 16; e += GTC_THREADS)
+  for (size_t e = tid; e < NPL * NST * arr_bytes / 16; e += GTC_THREADS)
     reinterpret_cast<uint4*>(gsm)[e] = make_uint4(0, 0, 0, 0);
   if (warp == 0) tmem_alloc(&tmem_base, tmem_cols);
   if (tid == 0) {
@@ -215,8 +228,8 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
             mine = false;
             break;
           }
-          unsigned char* hi = gsm + (size_t)s * 2 * arr_bytes;
-          unsigned char* lo = hi + arr_bytes;
+          unsigned char* p1 = gsm + (size_t)s * NPL * arr_bytes;  // pieces of this stage
+          unsigned char* p2 = p1 + arr_bytes;
 #pragma unroll
           for (int j = 0; j < UPT; ++j) {
             if (!act[j]) continue;
@@ -229,37 +242,30 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
               re[m] = v.x;
               im[m] = v.y;
             }
-            if (PREC == 0) {
-              uint4 hr, hm, lr, lm;
-              uint32_t* phr = &hr.x;
-              uint32_t* phm = &hm.x;
-              uint32_t* plr = &lr.x;
-              uint32_t* plm = &lm.x;
+            __align__(16) __nv_bfloat16 ar[8], ai[8], br[8], bi[8];
 #pragma unroll
-              for (int m = 0; m < 4; ++m) {
-                const uint32_t a = __float_as_uint(re[m]) & 0xFFFFE000u, b = __float_as_uint(im[m]) & 0xFFFFE000u;
-                phr[m] = a;
-                phm[m] = b;
-                plr[m] = __float_as_uint(re[m] - __uint_as_float(a));
-                plm[m] = __float_as_uint(im[m] - __uint_as_float(b));
-              }
-              *reinterpret_cast<uint4*>(hi + ore[j]) = hr;
-              *reinterpret_cast<uint4*>(hi + oim[j]) = hm;
-              *reinterpret_cast<uint4*>(lo + ore[j]) = lr;
-              *reinterpret_cast<uint4*>(lo + oim[j]) = lm;
-            } else {
-              __align__(16) __nv_bfloat16 hr[8], hm[8], lr[8], lm[8];
+            for (int m = 0; m < 8; ++m) {
+              ar[m] = __float2bfloat16_rn(re[m]);
+              ai[m] = __float2bfloat16_rn(im[m]);
+              re[m] -= __bfloat162float(ar[m]);  // exact: the remainder of a round-to-nearest
+              im[m] -= __bfloat162float(ai[m]);
+              br[m] = __float2bfloat16_rn(re[m]);
+              bi[m] = __float2bfloat16_rn(im[m]);
+            }
+            *reinterpret_cast<uint4*>(p1 + ore[j]) = *reinterpret_cast<const uint4*>(ar);
+            *reinterpret_cast<uint4*>(p1 + oim[j]) = *reinterpret_cast<const uint4*>(ai);
+            *reinterpret_cast<uint4*>(p2 + ore[j]) = *reinterpret_cast<const uint4*>(br);
+            *reinterpret_cast<uint4*>(p2 + oim[j]) = *reinterpret_cast<const uint4*>(bi);
+            if (PREC == 2) {
+              unsigned char* p3 = p2 + arr_bytes;
+              __align__(16) __nv_bfloat16 cr[8], ci[8];
 #pragma unroll
               for (int m = 0; m < 8; ++m) {
-                hr[m] = __float2bfloat16_rn(re[m]);
-                hm[m] = __float2bfloat16_rn(im[m]);
-                lr[m] = __float2bfloat16_rn(re[m] - __bfloat162float(hr[m]));
-                lm[m] = __float2bfloat16_rn(im[m] - __bfloat162float(hm[m]));
+                cr[m] = __float2bfloat16_rn(re[m] - __bfloat162float(br[m]));
+                ci[m] = __float2bfloat16_rn(im[m] - __bfloat162float(bi[m]));
               }
-              *reinterpret_cast<uint4*>(hi + ore[j]) = *reinterpret_cast<const uint4*>(hr);
-              *reinterpret_cast<uint4*>(hi + oim[j]) = *reinterpret_cast<const uint4*>(hm);
-              *reinterpret_cast<uint4*>(lo + ore[j]) = *reinterpret_cast<const uint4*>(lr);
-              *reinterpret_cast<uint4*>(lo + oim[j]) = *reinterpret_cast<const uint4*>(lm);
+              *reinterpret_cast<uint4*>(p3 + ore[j]) = *reinterpret_cast<const uint4*>(cr);
+              *reinterpret_cast<uint4*>(p3 + oim[j]) = *reinterpret_cast<const uint4*>(ci);
             }
           }
           fence_async_smem();
@@ -285,33 +291,38 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
       const int ep = it / GTC_EPOCH;
       if (it % GTC_EPOCH == 0 && ep > 0 && !gtc_wait(&accempty_b, (uint32_t)((ep - 1) & 1), &s_abort)) break;
       tc_fence_after();
-      const uint32_t hb = smem_u32(gsm + (size_t)s * 2 * arr_bytes), lb = hb + (uint32_t)arr_bytes;
+      const uint32_t b1 = smem_u32(gsm + (size_t)s * NPL * arr_bytes), b2 = b1 + (uint32_t)arr_bytes,
+                     b3 = b2 + (uint32_t)arr_bytes;
 #pragma unroll
-      for (int ks = 0; ks < GTC_KSTEP; ++ks) {
+      for (int ks = 0; ks < KSTEP; ++ks) {
         const uint32_t kb = (uint32_t)ks * 2 * LBO;
         // a new epoch overwrites the accumulator
         const uint32_t acc0 = (it % GTC_EPOCH || ks) ? 1u : 0u;
         uint32_t toff = 0;  // TMEM column of tile tt's first accumulator column
         for (int tt = 0; tt < ntile; ++tt) {
           const uint32_t arow = (uint32_t)(16 * tt) * SBO;  // rows 128 tt .. of X^T
-          const uint64_t ah = umma_desc(hb + arow + kb, LBO, SBO), al = umma_desc(lb + arow + kb, LBO, SBO);
+          const uint64_t a1 = umma_desc(b1 + arow + kb, LBO, SBO), a2 = umma_desc(b2 + arow + kb, LBO, SBO);
           const int w = R2C - 128 * tt;                      // columns [128 tt, 2Cp)
           const int np = (tt == 0 && w > 256) ? 2 : 1;       // N <= 256 per MMA
           const int pw = w / np;
-          const uint32_t idesc = umma_idesc(PREC == 0 ? 2u : 1u, 128, pw);
+          const uint32_t idesc = umma_idesc(1u, 128, pw);  // BF16 operands, FP32 accumulator
           for (int pc = 0; pc < np; ++pc) {
             const int c0 = 128 * tt + pc * pw;
             const uint32_t brow = (uint32_t)(c0 / 8) * SBO + kb;
-            const uint64_t bh = umma_desc(hb + brow, LBO, SBO), bl = umma_desc(lb + brow, LBO, SBO);
+            const uint64_t c1 = umma_desc(b1 + brow, LBO, SBO), c2 = umma_desc(b2 + brow, LBO, SBO);
             const uint32_t d = tmem + toff + (uint32_t)(pc * pw);
-            if (PREC == 0) {
-              umma_tf32(d, ah, bh, idesc, acc0);
-              umma_tf32(d, ah, bl, idesc, 1u);
-              umma_tf32(d, al, bh, idesc, 1u);
+            if (PREC == 2) {  // the small products first, then the leading one
+              const uint64_t a3 = umma_desc(b3 + arow + kb, LBO, SBO), c3 = umma_desc(b3 + brow, LBO, SBO);
+              umma_bf16(d, a1, c3, idesc, acc0);
+              umma_bf16(d, a2, c2, idesc, 1u);
+              umma_bf16(d, a3, c1, idesc, 1u);
+              umma_bf16(d, a1, c2, idesc, 1u);
+              umma_bf16(d, a2, c1, idesc, 1u);
+              umma_bf16(d, a1, c1, idesc, 1u);
             } else {
-              umma_bf16(d, ah, bh, idesc, acc0);
-              umma_bf16(d, ah, bl, idesc, 1u);
-              umma_bf16(d, al, bh, idesc, 1u);
+              umma_bf16(d, a1, c1, idesc, acc0);
+              umma_bf16(d, a1, c2, idesc, 1u);
+              umma_bf16(d, a2, c1, idesc, 1u);
             }
           }
           toff += (uint32_t)w;
@@ -424,14 +435,16 @@ __global__ void __launch_bounds__(GRED_T * 8) k_gram_tc_reduce(const float* __re
   }
 }
 
-static size_t gram_tc_smem_for(int C, int Ns, int r, int N, int periodic) {
-  return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16), periodic).total;
+static int gram_tc_prec(const smsm_plan_s* P) { return P->precision == SMSM_PRECISION_BF16_SPLIT ? 1 : 2; }
+
+static size_t gram_tc_smem_for(int C, int Ns, int r, int N, int periodic, int prec) {
+  return gtc_layout(Ns, N, r, 16 * ((C + 15) / 16), periodic, prec).total;
 }
 
 // 2Cp <= 288: the row tiles' accumulators take at most 480 TMEM columns; the ring and two
 // patch-row windows in shared memory
 int gram_tc_supported(const smsm_plan_s* P) {
-  return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic) <= 224 * 1024;
+  return P->C <= 144 && gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic, gram_tc_prec(P)) <= 224 * 1024;
 }
 
 int gram_tc_cp(const smsm_plan_s* P) { return 16 * ((P->C + 15) / 16); }
@@ -464,11 +477,11 @@ int gram_tc_nG(const smsm_plan_s* P) {
 }
 
 static size_t gram_tc_smem(const smsm_plan_s* P) {
-  return gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic);
+  return gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic, gram_tc_prec(P));
 }
 
 smsm_status gram_tc_init_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024);
   if (e != cudaSuccess) {
@@ -486,7 +499,7 @@ smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cu
     k_gram_tc<1><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
                                                                  nG, P->P1, P->periodic);
   else
-    k_gram_tc<0><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
+    k_gram_tc<2><<<grid, GTC_THREADS, gram_tc_smem(P), s>>>(x, P->Rpart, P->devflag, P->Ns, P->N, P->r, P->C, Cp,
                                                                  nG, P->P1, P->periodic);
   SMSM_LAUNCH_CHECK("k_gram_tc");
   const int nt = (P->C + GRED_T - 1) / GRED_T;

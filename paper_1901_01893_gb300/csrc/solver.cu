@@ -299,6 +299,7 @@ static smsm_plan_s lane_view(const smsm_plan_s* P, int d0, int nd, int lane) {
   v.Wf += cc;
   v.Gw += cc;
   v.Gw2 += cc;
+  v.Gw3 += cc;
   v.Gpart += cc * P->gram_nkx;
   v.eig += dd * L * Cp;
   v.rotlog += dd * L * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2);

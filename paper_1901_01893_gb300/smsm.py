@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsmsm.so")
 
 SMSM_OK, SMSM_ERR_ARG, SMSM_ERR_CUDA, SMSM_ERR_NOMEM = 0, 1, 2, 3
 SMSM_ERR_DIVERGED, SMSM_ERR_NOT_PD, SMSM_ERR_TIMEOUT, SMSM_ERR_STATE = 4, 5, 6, 7
+SMSM_ERR_EIG_UNCONVERGED = 8
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_FLAG_GENERIC_KERNELS = 1
 SMSM_FLAG_PER_COIL_NORMAL = 2
@@ -102,6 +103,24 @@ def lib() -> ctypes.CDLL:
     L.smsm_last_error.restype = ctypes.c_char_p
     L.smsm_default_params.argtypes = [ctypes.POINTER(Params)]
     L.smsm_default_params.restype = None
+    L.smsm_cnn_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i]
+    L.smsm_cnn_create.restype = st
+    L.smsm_cnn_destroy.argtypes = [vp]
+    L.smsm_cnn_destroy.restype = st
+    L.smsm_cnn_param_count.argtypes = [vp]
+    L.smsm_cnn_param_count.restype = ctypes.c_size_t
+    for fn in ("smsm_cnn_set_params", "smsm_cnn_get_params"):
+        getattr(L, fn).argtypes = [vp, vp, vp]
+        getattr(L, fn).restype = st
+    L.smsm_cnn_forward.argtypes = [vp, vp, vp, i, vp]
+    L.smsm_cnn_forward.restype = st
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.smsm_cnn_gradients.argtypes = [vp, vp, vp, i, vp, dp, vp]
+    L.smsm_cnn_gradients.restype = st
+    L.smsm_cnn_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, dp, vp]
+    L.smsm_cnn_train_step.restype = st
+    L.smsm_learned_start.argtypes = [vp, vp, vp, vp, vp]
+    L.smsm_learned_start.restype = st
     _lib = L
     return L
 
@@ -294,3 +313,68 @@ class Plan:
         return out
 
     fft2c = smsm_fft2c
+
+
+class CNN:
+    """The warm-start network: smsm_cnn_create(channels, width, layers, H, W, max_batch)."""
+
+    def __init__(self, channels: int, height: int, width_px: int, width: int = 64, layers: int = 6,
+                 max_batch: int = 1):
+        self.B, self.H, self.W, self.width, self.layers, self.maxn = channels, height, width_px, width, layers, max_batch
+        h = ctypes.c_void_p()
+        _check(lib().smsm_cnn_create(ctypes.byref(h), channels, width, layers, height, width_px, max_batch))
+        self._h = h
+        self.count = lib().smsm_cnn_param_count(h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().smsm_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _io(self, t: torch.Tensor, n: int, name: str) -> int:
+        return _dev(t, (n, self.B, self.H, self.W), name)
+
+    def set_params(self, p: torch.Tensor) -> None:
+        _check(lib().smsm_cnn_set_params(self._h, _dev(p, (self.count,), "params"), _stream()))
+
+    def get_params(self) -> torch.Tensor:
+        p = torch.empty(self.count, dtype=torch.complex64, device="cuda")
+        _check(lib().smsm_cnn_get_params(self._h, _dev(p, (self.count,), "params"), _stream()))
+        return p
+
+    def forward(self, a: torch.Tensor) -> torch.Tensor:
+        n = a.shape[0]
+        out = torch.empty_like(a)
+        _check(lib().smsm_cnn_forward(self._h, self._io(a, n, "a"), self._io(out, n, "x0"), n, _stream()))
+        return out
+
+    def gradients(self, a: torch.Tensor, t: torch.Tensor):
+        """(mean loss, gradient [count]) of the batch."""
+        n = a.shape[0]
+        g = torch.empty(self.count, dtype=torch.complex64, device=a.device)
+        loss = ctypes.c_double()
+        _check(lib().smsm_cnn_gradients(self._h, self._io(a, n, "a"), self._io(t, n, "t"), n,
+                                        _dev(g, (self.count,), "grad"), ctypes.byref(loss), _stream()))
+        return loss.value, g
+
+    def train_step(self, a: torch.Tensor, t: torch.Tensor, lr: float, want_loss: bool = True):
+        n = a.shape[0]
+        loss = ctypes.c_double()
+        _check(lib().smsm_cnn_train_step(self._h, self._io(a, n, "a"), self._io(t, n, "t"), n, float(lr),
+                                         ctypes.byref(loss) if want_loss else None, _stream()))
+        return loss.value if want_loss else None
+
+
+def learned_start(plan: "Plan", cnn: CNN, y: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
+    """x = F(cnn(F^-1(A^H y))), the learned starting point of every problem of the plan."""
+    if x is None:
+        x = torch.empty(plan.x_shape, dtype=torch.complex64, device=y.device)
+    _check(lib().smsm_learned_start(plan._h, cnn._h, _dev(y, plan.y_shape, "y"), _dev(x, plan.x_shape, "x"),
+                                    _stream()))
+    return x

@@ -2,12 +2,9 @@
 
 Tolerances (NRMSE = ||gpu - oracle|| / ||oracle||):
   * FP32 operators (forward, adjoint, fft2c, Gram, filter penalty): 1e-5.
-  * the whole IRLS + CG solve: 1e-3 (the metric's threshold).  Each outer
-    iteration re-derives W from an FP32 Gram whose rounding (~1e-7 s_max) is
-    amplified by (G + eps I)^(-1/2) up to (s_max / eps_min)-fold in the
-    null-space directions, and CG in FP32 amplifies it further by the
-    system's conditioning; 1e-3 is the threshold the throughput metric is
-    quoted at.
+  * the whole IRLS + CG solve, FP32 form: 1e-5 per slice (short schedules here;
+    the full schedules of the workloads are in test_gpu_solve_parity.py).
+  * reduced precision (BF16 split Gram): 1e-3, the metric's threshold.
 """
 import numpy as np
 import pytest
@@ -19,7 +16,14 @@ from paper_1901_01893_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
-SOLVE_TOL = 1e-3
+SOLVE_TOL = 1e-5   # per slice, FP32 form
+BF16_TOL = 1e-3
+
+
+def slice_err(x, ref):
+    """Largest per-slice NRMSE over the slices (and directions) of x."""
+    x = np.asarray(x)
+    return float(np.max(O.nrmse(x, ref, axis=tuple(range(x.ndim - 3, x.ndim)))))
 
 
 @pytest.fixture(scope="module")
@@ -195,7 +199,7 @@ def _problem(key, seed):
     return g, xt / sc, y / sc
 
 
-@pytest.mark.parametrize("key,K,J", [("tiny", 10, 10), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4),
+@pytest.mark.parametrize("key,K,J", [("tiny", 3, 4), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4),
                                      ("maxc", 2, 3), ("maxn", 2, 3)])
 def test_reconstruct_parity(smsm, key, K, J):
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -206,8 +210,8 @@ def test_reconstruct_parity(smsm, key, K, J):
     prm = smsm.default_params(lam=lam, outer_iters=K, cg_iters=J)
     x, rep = plan.reconstruct(c64(y), params=prm)
     assert rep.status == 0
-    err = O.nrmse(x.cpu().numpy(), ref)
-    print(f"{key}: reconstruct NRMSE vs oracle {err:.3e}; vs truth gpu {O.nrmse(x.cpu().numpy(), xt):.3e} "
+    err = slice_err(x.cpu().numpy(), ref)
+    print(f"{key}: reconstruct NRMSE vs oracle (worst slice) {err:.3e}; vs truth gpu {O.nrmse(x.cpu().numpy(), xt):.3e} "
           f"oracle {O.nrmse(ref, xt):.3e}")
     assert err < SOLVE_TOL
     # the graph is replayed on a second call with the same parameters: identical result
@@ -225,7 +229,9 @@ def test_reconstruct_nullspace_mode(smsm):
     prm = smsm.default_params(lam=1e-1, outer_iters=3, cg_iters=5, mode=smsm.SMSM_MODE_NULLSPACE, rank=rank)
     x, rep = plan.reconstruct(c64(y), params=prm)
     assert rep.status == 0
-    assert O.nrmse(x.cpu().numpy(), ref) < SOLVE_TOL
+    err = slice_err(x.cpu().numpy(), ref)
+    print(f"nullspace mode: worst slice NRMSE vs oracle {err:.3e}")
+    assert err < SOLVE_TOL
 
 
 def test_reconstruct_warm_start_and_lambda0(smsm):
@@ -240,7 +246,7 @@ def test_reconstruct_warm_start_and_lambda0(smsm):
     plan, _, _ = make_plan(smsm, key, sens=g["sens"])
     prm = smsm.default_params(lam=0.0, outer_iters=2, cg_iters=4, warm=1)
     x, rep = plan.reconstruct(c64(y), x=c64(x0), params=prm)
-    assert O.nrmse(x.cpu().numpy(), ref) < 1e-4
+    assert slice_err(x.cpu().numpy(), ref) < SOLVE_TOL
 
 
 def test_errors_do_not_abort(smsm):
@@ -295,9 +301,9 @@ def test_batch_matches_single_problems(smsm):
     p1.set_sens(c64(g["sens"]))
     for d in range(D):
         x1, _ = p1.reconstruct(c64(ys[d]), params=prm)
-        assert O.nrmse(xb_out[d].cpu().numpy(), x1.cpu().numpy()) < 1e-4
+        assert slice_err(xb_out[d].cpu().numpy(), x1.cpu().numpy()) < SOLVE_TOL
     ref = O.reconstruct(ys[D - 1], g["sens"], r, dict(K=4, J=5, lam=1e-2), Ldiv=Ldiv)
-    assert O.nrmse(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
+    assert slice_err(xb_out[D - 1].cpu().numpy(), ref) < SOLVE_TOL
 
 
 def test_periodic_boundary_parity(smsm):
@@ -324,8 +330,8 @@ def test_periodic_boundary_parity(smsm):
     xo, rep = p.reconstruct(c64(y), params=prm)
     assert rep.status == 0
     ref = O.reconstruct(y, g["sens"], r, dict(K=3, J=4, lam=1e-2, periodic=True), Ldiv=Ldiv)
-    err = O.nrmse(xo.cpu().numpy(), ref)
-    print(f"periodic: reconstruct NRMSE vs oracle {err:.3e}")
+    err = slice_err(xo.cpu().numpy(), ref)
+    print(f"periodic: reconstruct NRMSE vs oracle (worst slice) {err:.3e}")
     assert err < SOLVE_TOL
 
 
@@ -347,8 +353,8 @@ def test_sms_sense_parity(smsm, with_phase):
     x = x.cpu().numpy()
     for d in range(D):
         ref = O.sense(ys[d], g["sens"], L, J, phase=ph[d] if with_phase else None, Ldiv=Ldiv)
-        err = O.nrmse(x[d], ref)
-        assert err < 1e-4, err
+        err = slice_err(x[d], ref)
+        assert err < SOLVE_TOL, err
 
 
 def test_groups_of_different_geometry_match_single_solves(smsm):
@@ -424,7 +430,7 @@ def test_fast_column_stage_matches_generic(smsm, L, Ns, Nc, N, r, Ldiv):
     assert O.nrmse(out[1], out[2]) < 1e-5
     if N <= 128:
         ref = O.reconstruct(y, S, r, dict(K=2, J=3, lam=3e-2), Ldiv=Ldiv or L)
-        assert O.nrmse(out[0], ref) < 1e-4
+        assert slice_err(out[0], ref) < SOLVE_TOL
 
 
 def test_warm_started_eigensolver_matches_cold(smsm):
@@ -441,7 +447,7 @@ def test_warm_started_eigensolver_matches_cold(smsm):
         assert rep.status == 0
         out.append((x.cpu().numpy(), [rep.sweeps[k] for k in range(4)]))
     print("sweeps warm", out[0][1], "cold", out[1][1])
-    assert O.nrmse(out[0][0], out[1][0]) < 1e-4
+    assert slice_err(out[0][0], out[1][0]) < SOLVE_TOL
     assert sum(out[0][1][1:]) < sum(out[1][1][1:])  # warm starts need fewer sweeps
 
 
@@ -479,6 +485,6 @@ def test_bf16_split_precision_form(smsm):
     p.set_sens(c64(g["sens"]))
     xr, rep = p.reconstruct(c64(y), params=smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4))
     assert rep.status == 0
-    err = O.nrmse(xr.cpu().numpy(), ref)
-    print("BF16 split solve NRMSE vs FP64 oracle", err)
-    assert err < SOLVE_TOL
+    err = slice_err(xr.cpu().numpy(), ref)
+    print("BF16 split solve NRMSE vs FP64 oracle (worst slice)", err)
+    assert err < BF16_TOL
