@@ -3,12 +3,17 @@
 A step is one complete reconstruction of one slice group (every row of the
 hot path: A^H y, then K outer iterations of Gram -> Jacobi eigen-decomposition
 -> weights -> filters -> J CG steps of (A^H A + lambda P_W)) through the C ABI.
-The workload is the plain FP32 configuration: MB=2 slices, 4 interleaved
-shots, 32 coils, 128x128, filter 6x6, 20 outer x 15 CG iterations, seeded
-synthetic data (ellipse phantom, polynomial + band-limited shot phase, ring
-coil maps, SNR 30).
+The default workload is the plain FP32 configuration: MB=2 slices, 4
+interleaved shots, 32 coils, 128x128, FOV/2 CAIPI shift, filter 6x6, 20 outer
+x 15 CG iterations, seeded synthetic data (ellipse phantom, polynomial +
+band-limited shot phase, ring coil maps, SNR 30); ``--workload precision`` is
+MB=3, 256x256, FOV/3 (with ``--precision bf16-split`` for the BF16 hi+lo
+split Gram).  The FP64 oracle's full reconstruction of direction 0 runs on
+the host cores meanwhile: its time is the CPU baseline and its result checks
+the accuracy (per-slice NRMSE) of direction 0 of the timed batch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload plain|precision] [--precision fp32|bf16-split]
 
 Multi-GPU: slice groups are independent, so every rank reconstructs its own
 groups (replicas, weak scaling); the host only gathers the timings.
@@ -33,13 +38,15 @@ from paper_1901_01893_gb300 import synth  # noqa: E402
 
 METRIC = "slice-group recons/sec at NRMSE≤1e-3 vs FP64 oracle: learned+BF16+batched vs plain"
 UNIT = "slice-groups/s"
-WORKLOAD = "plain"
 LAM = 1e-2
+ACCURACY_BAR = 1e-3  # per-slice NRMSE vs the FP64 oracle at which the metric is quoted
+# CAIPI FOV shift per workload: FOV/2 for the two-slice workloads, FOV/3 for MB 3
+LDIV = {"tiny": 2, "plain": 2, "precision": 3}
 
 
-def workload_desc(c, D=1):
-    return (f"plain FP32 form: MB={c['L']} slices, {c['Ns']} interleaved shots, {c['Nc']} coils, "
-            f"{c['N']}x{c['N']}, filter {c['r']}x{c['r']}, {c['K']} outer x {c['J']} CG; "
+def workload_desc(c, D=1, name="plain"):
+    return (f"{name} workload: MB={c['L']} slices, {c['Ns']} interleaved shots, {c['Nc']} coils, "
+            f"{c['N']}x{c['N']}, FOV/{LDIV[name]} CAIPI shift, filter {c['r']}x{c['r']}, {c['K']} outer x {c['J']} CG; "
             f"{D} diffusion directions of one slice group per step (shared coil maps, independent shot phase)")
 
 
@@ -70,34 +77,40 @@ def throughput(world: int, batch: int, ms_per_step: float) -> float:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle timing (bounded sample, extrapolated to one reconstruction)
+# The FP64 oracle: the CPU baseline, the reference arm and the accuracy check.
+# Only these functions touch oracle/; they run in a spawned worker process or
+# after every GPU measurement, never on the GPU path.
 # ---------------------------------------------------------------------------
 
-def oracle_sample(cfg, y, sens, reps=1):
-    """Time the oracle on a bounded sample of the reconstruction and extrapolate one
-    full reconstruction: A^H y once, then `reps` complete outer iterations (Gram,
-    eigen-decomposition and weights, J CG steps of A^H A + lam P_W) from A^H y;
-    T = T(A^H y) + K * median T(outer iteration)."""
+def oracle_data(cfg, seed, Ldiv):
+    """Direction 0's slice group and its data y = A x_true + noise (SNR 30),
+    normalised to RMS |y| = 1, synthesised on the host by the oracle."""
     import oracle as O
 
-    r, K, J = cfg["r"], cfg["K"], cfg["J"]
-    L = sens.shape[0]
+    g = make_host_inputs(cfg, seed)
+    _, y = O.make_data(g, cfg["snr"], Ldiv=Ldiv)
+    return g, y / np.sqrt(np.mean(np.abs(y) ** 2))
+
+
+def oracle_full_solve(cfg, y, sens, Ldiv):
+    """One complete oracle reconstruction (K outer x J CG); returns (x, wall seconds,
+    threads).  Run in a spawned worker while the GPU is measured."""
+    import oracle as O
+
     t0 = time.perf_counter()
-    b = O.adjoint(y, sens, L)
-    ta = time.perf_counter() - t0
-    touter = []
-    for _ in range(reps):
-        t1 = time.perf_counter()
-        G = O.gram(b, r)
-        W, s = O.irls_weight(G, 1e-2 * max(np.max(x) for x in np.linalg.eigvalsh(G)))
-        O.cg(lambda v: O.normal(v, sens) + LAM * O.penalty(v, W, r), b, b.copy(), J)
-        touter.append(time.perf_counter() - t1)
-    to = statistics.median(touter)
-    total = ta + K * to
-    sample = (f"oracle (NumPy FP64, explicit Hankel) on the same workload: timed A^H y and {reps} complete outer "
-              f"iterations (Gram + eigh + W, {J} CG steps), median extrapolated to {K} outer iterations "
-              f"(sample {ta + sum(touter):.1f} s, full recon {total:.0f} s)")
-    return total, sample
+    x = O.reconstruct(y, sens, cfg["r"], dict(K=cfg["K"], J=cfg["J"], lam=LAM), Ldiv=Ldiv)
+    return x, time.perf_counter() - t0, cpu_threads()
+
+
+def oracle_step(cfg, y, sens, Ldiv):
+    """The reference arm's step: A^H y and the first outer iteration of the oracle's
+    reconstruction (Gram, eigen-decomposition and weights on the real eps schedule,
+    J CG steps).  Returns its wall seconds."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    O.reconstruct(y, sens, cfg["r"], dict(K=1, J=cfg["J"], lam=LAM), Ldiv=Ldiv)
+    return time.perf_counter() - t0
 
 
 def cpu_threads():
@@ -105,7 +118,7 @@ def cpu_threads():
         from threadpoolctl import threadpool_info
 
         n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
-        return int(n)
+        return int(max(n, os.cpu_count() or 1))
     except Exception:
         return os.cpu_count() or 1
 
@@ -119,25 +132,23 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    import oracle as O
-
-    cfg = dict(synth.CONFIGS[WORKLOAD])
-    g = make_host_inputs(cfg, cfg["seed"])
-    xt, y = O.make_data(g, cfg["snr"])
-    y = y / np.sqrt(np.mean(np.abs(y) ** 2))
+    name = args.workload
+    cfg = dict(synth.CONFIGS[name])
+    g, y = oracle_data(cfg, cfg["seed"], LDIV[name])
     for _ in range(args.warmup):
-        oracle_sample(cfg, y, g["sens"])
-    per = []
-    for _ in range(args.steps):
-        t, sample = oracle_sample(cfg, y, g["sens"])
-        per.append(t)
+        oracle_step(cfg, y, g["sens"], LDIV[name])
+    per = [oracle_step(cfg, y, g["sens"], LDIV[name]) for _ in range(args.steps)]
     t = statistics.mean(per)
-    v = 1.0 / t
+    v = 1.0 / (cfg["K"] * t)
+    sample = (f"each step: A^H y and the first of the {cfg['K']} outer iterations (Gram + eigh + W on the "
+              f"oracle's eps schedule, {cfg['J']} CG steps) of one direction's FP64 oracle reconstruction, "
+              f"{t:.2f} s; value = 1 / ({cfg['K']} x step time), the outer iterations extrapolated")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_desc(cfg), "form": "FP64 CPU oracle"},
+        "config": {"workload": workload_desc(cfg, 1, name), "form": "FP64 CPU oracle",
+                   "step": "one outer iteration of one direction (see cpu_baseline.sample)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -200,16 +211,11 @@ class Clocks:
 # our arm
 # ---------------------------------------------------------------------------
 
-# DRAM bytes (read + write) per direction of one launch of each kernel class, from the
-# ncu captures summarised in profiles/ (plain workload, 26-direction launches divided by
-# 26; the traffic of these kernels grows in proportion to the directions a launch covers).
-# Only valid for the kernels as captured: a class whose kernel changes is dropped here.
-TRAFFIC_PER_DIRECTION = {
-    "eig": (8.665088e6 + 0.532992e6) / 26,      # profiles/k_jacobi_plain_128.md
-    "gram": (27.687680e6 + 78.208256e6) / 26,   # profiles/k_gram_tc_plain_128.md
-    "column": (97.608704e6 + 8.169728e6) / 26,  # profiles/k_col_alias_plain_128.md
-    "vapply": (38.639616e6 + 0.875264e6) / 26,  # profiles/k_vapply_plain_128.md
-}
+# DRAM bytes (read + write) per direction of one launch of a kernel class, measured
+# by ncu on the current kernels ({workload: {class: bytes}}; a launch covering d
+# directions moves d times this).  A class whose kernel changed since its capture is
+# left out, so its roofline line carries traffic = null.
+TRAFFIC_PER_DIRECTION: dict = {}
 
 
 def stage_work(cfg, D, sweeps):
@@ -233,7 +239,8 @@ def stage_work(cfg, D, sweeps):
         "band": ("alu", D * 8 * L * nband * Ns * Ns * R2 * R2),
         "gram": ("alu", D * 8 * L * P * C * (C + 1) / 2),
         "eig": ("alu", D * L * sweeps * (Cp - 1) * (half * (half + 1) / 2) * 96),
-        "vapply": ("alu", D * L * sweeps * (Cp - 1) * half * C * 18),
+        # rotation replay on V's rows, then the Newton-Schulz step (two C x C complex products)
+        "vapply": ("alu", D * L * (sweeps * (Cp - 1) * half * C * 18 + 2 * 8 * C ** 3)),
         "rowfft_inv": ("hbm", D * 2 * 8 * B * NN),
         "rowfft_fwd": ("hbm", D * 2 * 8 * B * NN),
         "cg": ("hbm", D * 9 * 8 * B * NN),
@@ -249,6 +256,26 @@ def run_ours(args):
     import torch
 
     rank, world, local = env_rank()
+    name = args.workload
+    cfg = dict(synth.CONFIGS[name])
+    Ldiv = LDIV[name]
+    L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
+    seed = seed_for_rank(cfg["seed"], rank)
+    D = args.batch
+
+    # CPU baseline and accuracy check (rank 0 at N = 1): direction 0's data is made on the
+    # host by the oracle, and its full oracle reconstruction runs in a spawned worker on the
+    # host cores while the GPU is measured.
+    oracle_leg = world == 1 and not args.no_cpu_baseline
+    pool = fut = None
+    if oracle_leg:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        g0h, y0h = oracle_data(cfg, seed, Ldiv)
+        pool = cf.ProcessPoolExecutor(max_workers=1, mp_context=mp.get_context("spawn"))
+        fut = pool.submit(oracle_full_solve, cfg, y0h, g0h["sens"], Ldiv)
+
     if world > 1:
         import torch.distributed as dist
 
@@ -260,14 +287,10 @@ def run_ours(args):
     _build.build()
     from paper_1901_01893_gb300 import smsm
 
-    cfg = dict(synth.CONFIGS[WORKLOAD])
-    L, Ns, Nc, N, r = cfg["L"], cfg["Ns"], cfg["Nc"], cfg["N"], cfg["r"]
-    seed = seed_for_rank(cfg["seed"], rank)
-    D = args.batch
     c64 = lambda a: torch.from_numpy(np.ascontiguousarray(a).astype(np.complex64)).to(dev)  # noqa: E731
     prec = smsm.SMSM_PRECISION_BF16_SPLIT if args.precision == "bf16-split" else smsm.SMSM_PRECISION_FP32
-    plan = smsm.Plan(L, Ns, Nc, N, r, batch=D, precision=prec)
-    one = smsm.Plan(L, Ns, Nc, N, r)  # synthesis, one direction at a time
+    plan = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D, precision=prec)
+    one = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv)  # synthesis, one direction at a time
     ys = []
     for d in range(D):
         g = make_host_inputs(cfg, seed + d)  # same coil maps for every seed; own phantom, phase, noise
@@ -276,6 +299,9 @@ def run_ours(args):
             plan.set_sens(c64(sens0))
             one.set_sens(c64(sens0))
             g0 = g
+        if d == 0 and oracle_leg:
+            ys.append(c64(y0h))
+            continue
         # synthesis on the GPU: x_rho = F_c(rho); y = A(x_rho; phi) + noise at SNR 30; RMS(y) = 1
         xr = one.fft2c(c64(g0["rho"][:, None]))  # one object, imaged along every direction
         yc = one.forward(xr, phase=c64(g["phase"]))
@@ -283,7 +309,6 @@ def run_ours(args):
         yd = yc + nz * (torch.linalg.vector_norm(yc) / (cfg["snr"] * torch.linalg.vector_norm(nz)))
         ys.append(yd / torch.sqrt(torch.mean(torch.abs(yd) ** 2)))
     y = (torch.stack(ys) if D > 1 else ys[0]).contiguous()
-    g = g0
     x = torch.empty(plan.x_shape, dtype=torch.complex64, device=dev)
 
     allmask = (1 << len(smsm.STAGES)) - 1
@@ -304,7 +329,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    dom_ms, dom_n, launches = 0.0, 0, 0
+    dom_ms, dom_n, launches, status = 0.0, 0, 0, 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -317,15 +342,17 @@ def run_ours(args):
             dom_ms += rep.stage_ms[smsm.STAGE[dominant]]
             dom_n += rep.stage_launches[smsm.STAGE[dominant]]
             launches += rep.graph_kernels
-            if rep.status != 0:
-                raise RuntimeError(f"solve reported status {rep.status}")
+            status = status or rep.status
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    if status not in (0, smsm.SMSM_ERR_EIG_UNCONVERGED):
+        raise RuntimeError(f"solve reported status {status}")
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     clocks = clk.summary()
     ms = max_over_ranks(ms, dev)
     value = throughput(world, D, ms)
+    x_dir0 = (x[0] if D > 1 else x).cpu().numpy()
 
     # end to end through the public API: pinned host y -> device, solve, x -> pinned host
     y_host = y.cpu().pin_memory()
@@ -360,7 +387,7 @@ def run_ours(args):
     # timed brackets cover the launches of lane 0, each over its sub-batch of directions
     d_launch = rep.lane0_batch if rep.lanes > 1 else D
     bound, amount = stage_work(cfg, d_launch, sweeps)[dominant]
-    tpd = TRAFFIC_PER_DIRECTION.get(dominant) if WORKLOAD == "plain" else None
+    tpd = TRAFFIC_PER_DIRECTION.get(name, {}).get(dominant)
     traffic = tpd * d_launch if tpd is not None else None
     per_launch_ms = dom_ms / max(dom_n, 1)
     sm_mhz = clocks.get("sm_mhz") or 1455.0
@@ -376,27 +403,38 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                 "traffic": traffic, "kernel": dominant, "launch_ms": per_launch_ms, "peak_note": peak_src}
 
-    # CPU baseline: the oracle as it stands, on a bounded sample of the same workload
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        import oracle as O  # noqa: F401
+    # CPU baseline and accuracy: the oracle's full reconstruction of direction 0
+    cpu, acc, acc_ok = None, None, True
+    if fut is not None:
+        import oracle as O
 
-        y_np = (y[0] if D > 1 else y).cpu().numpy().astype(np.complex128)
-        t_cpu, sample = oracle_sample(cfg, y_np, g["sens"], reps=5)
-        cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample}
+        ref, t_or, thr = fut.result()
+        pool.shutdown()
+        e = O.nrmse(x_dir0, ref, axis=(1, 2, 3))
+        acc_ok = bool(np.max(e) <= ACCURACY_BAR)
+        acc = {"per_slice": [float(v) for v in e], "max": float(np.max(e)), "bar": ACCURACY_BAR,
+               "direction": 0, "K": cfg["K"], "J": cfg["J"],
+               "what": "direction 0 of the timed batch against the FP64 oracle's reconstruction of the same data "
+                       "(same K, J, lambda and eps schedule), per slice"}
+        cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": (f"one complete FP64 oracle reconstruction (NumPy, explicit Hankel; {cfg['K']} outer x "
+                          f"{cfg['J']} CG) of direction 0, {t_or:.1f} s wall on the host cores, run while the GPU "
+                          f"was measured; not extrapolated")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+bf16-split",
         "data": "synthetic",
-        "config": {"workload": workload_desc(cfg, D),
+        "config": {"workload": workload_desc(cfg, D, name),
                    "form": ("plain FP32 (FP64 reductions)" if args.precision == "fp32" else
                             "BF16 hi+lo split Hankel Gram, FP32 elsewhere (FP64 reductions)"),
                    "directions_per_step": D, "lanes": rep.lanes,
                    "l2": "flushed before every step (512 MB write)", "parallelism": f"replicas x{world}",
                    "lambda": LAM, "stages_ms_first_warmup": stages_all,
-                   "jacobi_sweeps_per_outer": [rep.sweeps[k] for k in range(cfg["K"])]},
+                   "jacobi_sweeps_per_outer": [rep.sweeps[k] for k in range(cfg["K"])],
+                   "eig_status": int(status)},
+        "nrmse_vs_oracle": acc,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": throughput(world, D, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(y.numel() * 8),
@@ -407,6 +445,9 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    if not acc_ok:
+        sys.exit(f"accuracy check failed: direction 0 per-slice NRMSE vs the FP64 oracle {acc['per_slice']} "
+                 f"above {ACCURACY_BAR}")
 
 
 def main():
@@ -415,7 +456,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the oracle leg (CPU baseline and the accuracy check of direction 0)")
+    ap.add_argument("--workload", default="plain", choices=["plain", "precision"],
+                    help="plain: MB 2, 4 shots, 32 coils, 128^2, FOV/2; precision: MB 3, 4 shots, 32 coils, "
+                         "256^2, FOV/3 (both filter 6x6, 20 outer x 15 CG)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16-split"],
                     help="Hankel Gram form: FP32-accurate TF32 split (default) or the BF16 hi+lo split")
     ap.add_argument("--lanes", type=int, default=0,

@@ -115,7 +115,8 @@ typedef struct {
   double lambda;      /* penalty weight in the normal equations (default 1e-2) */
   double eps0_rel;    /* default 1e-2 */
   double eta;         /* default 1.5 */
-  double eps_min_rel; /* default 1e-4 */
+  double eps_min_rel; /* default 1e-2: eps_min = 1e-4 s_max, so the weights (s + eps)^(-1/2)
+                         span at most a factor 100, the range the FP32 penalty represents */
   int outer_iters;    /* K, default 10, at most SMSM_MAX_OUTER */
   int cg_iters;       /* J, default 10 */
   int mode;           /* smsm_mode */
@@ -289,14 +290,18 @@ smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, i
  * the allocator -- and so cannot call smsm_plan, which allocates).
  *   x: [mb][shots][n][n] complex64, G: [mb][C][C] complex128, C = shots*filter^2,
  *   same definition and layouts as smsm_hankel_gram; 1 <= shots <= 8,
- *   16 <= n <= 512, 1 <= filter <= min(12, n/2).
- * Scratch: one fixed 8 MiB array compiled into the library (held by every GPU
- * that loads it until exit).  Geometries needing more than
+ *   16 <= n <= 512, 1 <= filter <= min(12, n/2), C <= 320.
+ * Scratch: one fixed 8 MiB array compiled into the library, held by every GPU
+ * that loads the library's device code until exit (with lazy module loading,
+ * from the first call of this entry point or the first launch of any of the
+ * library's kernels on that GPU).  Geometries needing more than
  * ceil((n-filter+1)/16) * C^2 * 16 bytes > 8 MiB are rejected with
- * SMSM_ERR_ARG.  All calls on a device share that array: calls that overlap
- * on the GPU race and must be serialised by the caller.  Nothing in it needs
- * clearing between calls.  The first call on a device looks the array's
- * address up; make it before any stream capture on that device.
+ * SMSM_ERR_ARG, as is C > 320.  All calls on a device share that array: calls
+ * that overlap on the GPU race and must be serialised by the caller.  Nothing
+ * in it needs clearing between calls.  Every call looks the array's address
+ * up in the current context; the first call on a device may load the
+ * library's device code, so make it once at set-up, before any stream capture
+ * on that device.
  */
 smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, int n, int filter,
                                      void* stream);
@@ -340,11 +345,12 @@ smsm_status smsm_cnn_gradients(smsm_cnn_t cnn, const void* a, const void* t, int
  * the batch's loss. */
 smsm_status smsm_cnn_train_step(smsm_cnn_t cnn, const void* a, const void* t, int n, float lr, double* loss,
                                 void* stream);
-/* The learned starting point of every problem of `plan`: x = F(cnn(F^-1(A^H y))),
- * y [D][Ns][Nc][N/Ns][N], x [D][L][Ns][N][N] (the layouts of smsm_reconstruct).
- * Needs cnn channels = L*Ns, an N x N image and max_batch >= D.  Pass x to
- * smsm_reconstruct with params->warm = 1. */
-smsm_status smsm_learned_start(smsm_plan_t plan, smsm_cnn_t cnn, const void* y, void* x, void* stream);
+/* The learned refinement of a k-space estimate for every problem of `plan`:
+ * x_out = F(cnn(F^-1(x_in))), x_in and x_out [D][L][Ns][N][N] (the layout of x in
+ * smsm_reconstruct; they may alias).  x_in is A^H y (smsm_adjoint) or an early iterate
+ * of smsm_reconstruct; pass x_out to smsm_reconstruct with params->warm = 1.  Needs cnn
+ * channels = L*Ns, an N x N image and max_batch >= D. */
+smsm_status smsm_learned_start(smsm_plan_t plan, smsm_cnn_t cnn, const void* x_in, void* x_out, void* stream);
 
 /*
  * Synchronise `stream` and report the plan's device error flag: SMSM_OK, or

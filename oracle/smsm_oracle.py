@@ -266,7 +266,7 @@ def cg(apply_N, b: np.ndarray, x: np.ndarray, J: int) -> tuple[np.ndarray, list[
 # The reconstruction (Eq. 10 by IRLS + CG)
 # ---------------------------------------------------------------------------
 
-DEFAULT_PARAMS = dict(lam=1e-2, eps0_rel=1e-2, eta=1.5, eps_min_rel=1e-4, K=10, J=10,
+DEFAULT_PARAMS = dict(lam=1e-2, eps0_rel=1e-2, eta=1.5, eps_min_rel=1e-2, K=10, J=10,
                       mode="irls", rank=0, periodic=False)
 
 

@@ -18,8 +18,10 @@
 // rotations but two things around them:
 //  * no rotation is skipped because it is small next to the largest eigenvalue:
 //    W = (G + eps I)^(-1/2) is largest on the smallest eigenvalues (down to eps_min),
-//    so off-diagonal entries far below s_max still move W there.  The only absolute
-//    floor is tied to eps_min (a thousandth of it), where W no longer changes;
+//    so off-diagonal entries far below s_max still move W there (an entry delta left
+//    in place changes W by about delta / (2 eps) relative).  The only absolute floor
+//    is 1e-12 of the largest diagonal entry, which stops rounding noise between
+//    exactly zero eigenvalues from churning;
 //  * V stays orthonormal: the rotations of one eigen step (and the warm starts from
 //    the previous V) would otherwise add their rounding to V's orthogonality from
 //    one outer iteration to the next.  After every eigen step V is re-orthonormalised
@@ -118,8 +120,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   __syncthreads();
   if (tid < Cp) atomicMax(reinterpret_cast<int*>(&dmax), __float_as_int(fmaxf(g[tid * ld + tid].x, 0.f)));
   __syncthreads();
-  // absolute floor of the rotation test: a thousandth of eps_min (given relative to the
-  // largest diagonal entry), far below every eigenvalue that W resolves
+  // absolute floor of the rotation test (given relative to the largest diagonal entry)
   const float floor_abs = floor_rel * dmax;
   // this thread's blocks of the folded triangle, the same in every round
   int kb1[JAC_BLK], kb2[JAC_BLK];
@@ -337,82 +338,42 @@ __global__ void __launch_bounds__(32 * VA_WARPS) k_vapply(const float4* __restri
   }
 }
 
-// Warm start: Gw = V^H G V, the previous eigenvectors' Rayleigh-Ritz projection of the new
-// Gram, formed in double-FP32 arithmetic so that its small entries -- the block of the
-// smallest eigenvalues, where W = (G + eps I)^(-1/2) is largest -- are accurate relative
-// to themselves, not only to s_max: every product is split exactly (a * b = p + e with
-// e = fma(a, b, -p)) and summed into a (hi, lo) pair with an error-free two-sum.
-// step 0: T = G V (G in FP64 as hi + lo FP32, V in FP32) -> (Thi, Tlo);
-// step 1: Gw = V^H (Thi + Tlo), rounded once to FP32.
-struct Df {  // hi + lo, |lo| <= ulp(hi)/2 after each add
-  float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(Df& s, float a, float b) {
-  const float p = a * b;
-  const float e = fmaf(a, b, -p);
-  const float t = s.hi + p;
-  const float bb = t - s.hi;
-  const float err = (s.hi - (t - bb)) + (p - bb);
-  s.hi = t;
-  s.lo += err + e;
-}
+// Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
+// step 0: T = G V (G in FP64, rounded on load); step 1: Gw = V^H T.
 __global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ G, const float2* __restrict__ V,
-                                                    const float2* __restrict__ Thi, const float2* __restrict__ Tlo,
-                                                    float2* __restrict__ out, float2* __restrict__ out_lo, int C,
+                                                    const float2* __restrict__ Tin, float2* __restrict__ out, int C,
                                                     int step) {
-  __shared__ float2 Ah[CG_T][CG_T + 1], Al[CG_T][CG_T + 1];
-  __shared__ float2 Bh[CG_T][CG_T + 1], Bl[CG_T][CG_T + 1];
+  __shared__ float2 As[CG_T][CG_T + 1];
+  __shared__ float2 Bs[CG_T][CG_T + 1];
   const int l = blockIdx.z;
   const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
   const int a = blockIdx.y * CG_T + ty, b = blockIdx.x * CG_T + tx;
   const size_t off = (size_t)l * C * C;
-  Df re{0.f, 0.f}, im{0.f, 0.f};
+  float2 acc = cmk(0.f, 0.f);
   for (int k0 = 0; k0 < C; k0 += CG_T) {
+    // A tile: rows a-block, cols k;  B tile: rows k, cols b-block
     const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
     const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
-    float2 ah = cmk(0.f, 0.f), al = cmk(0.f, 0.f), bh = cmk(0.f, 0.f), bl = cmk(0.f, 0.f);
+    float2 av = cmk(0.f, 0.f), bv = cmk(0.f, 0.f);
     if (ar < C && ak < C) {
       if (step == 0) {
         const double2 gv = G[off + (size_t)ar * C + ak];
-        ah = cmk((float)gv.x, (float)gv.y);
-        al = cmk((float)(gv.x - (double)ah.x), (float)(gv.y - (double)ah.y));
+        av = cmk((float)gv.x, (float)gv.y);
       } else {
-        ah = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
+        av = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
       }
     }
-    if (bk < C && bc < C) {
-      if (step == 0) {
-        bh = V[off + (size_t)bk * C + bc];
-      } else {
-        bh = Thi[off + (size_t)bk * C + bc];
-        bl = Tlo[off + (size_t)bk * C + bc];
-      }
-    }
-    Ah[ty][tx] = ah;
-    Al[ty][tx] = al;
-    Bh[ty][tx] = bh;
-    Bl[ty][tx] = bl;
+    if (bk < C && bc < C) bv = step == 0 ? V[off + (size_t)bk * C + bc] : Tin[off + (size_t)bk * C + bc];
+    As[ty][tx] = av;
+    Bs[ty][tx] = bv;
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < CG_T; ++k) {
-      const float2 x = Ah[ty][k], y = Bh[k][tx];
-      df_add_prod(re, x.x, y.x);
-      df_add_prod(re, -x.y, y.y);
-      df_add_prod(im, x.x, y.y);
-      df_add_prod(im, x.y, y.x);
-      // the low parts: products of small terms, rounded once
-      const float2 xl = Al[ty][k], yl = Bl[k][tx];
-      re.lo = fmaf(xl.x, y.x, fmaf(-xl.y, y.y, fmaf(x.x, yl.x, fmaf(-x.y, yl.y, re.lo))));
-      im.lo = fmaf(xl.x, y.y, fmaf(xl.y, y.x, fmaf(x.x, yl.y, fmaf(x.y, yl.x, im.lo))));
-    }
+#pragma unroll
+    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
     __syncthreads();
   }
-  if (a < C && b < C) {
-    const float rh = re.hi + re.lo, ih = im.hi + im.lo;
-    out[off + (size_t)a * C + b] = cmk(rh, ih);
-    if (step == 0) out_lo[off + (size_t)a * C + b] = cmk((re.hi - rh) + re.lo, (im.hi - ih) + im.lo);
-  }
+  if (a < C && b < C) out[off + (size_t)a * C + b] = acc;
 }
+
 
 // Newton-Schulz re-orthonormalisation of V (one step squares the orthogonality error):
 // step 0: M = V^H V;  step 1: out = V (3I - M) / 2.  16 x 16 output tiles, FP32.
@@ -485,12 +446,16 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
 
 // W[a][b] = sum_j V[a][j] f_j conj(V[b][j]), f_j = (max(s_j, 0) + eps)^(-1/2) (IRLS) or
 // [s_j among the C - rank smallest] (NULLSPACE).  16 x 16 output tiles, K tiles of 16.
+// The weights span up to sqrt(s_max / eps_min), and W's entries carry the largest of
+// them while the penalty needs W's action on the directions of the smallest: so the sum
+// is accumulated in double-FP32 (f_j conj(V[b][j]) formed in FP64 and split into hi + lo,
+// the products with V[a][j] taken exactly) and W is returned as hi (Wf) + lo (Wlo).
 __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, const float* __restrict__ eig,
-                                                 const SolverState* __restrict__ st, float2* __restrict__ W, int C,
-                                                 int Cp, int mode, int rank, int L) {
-  __shared__ float f[SMSM_MAX_C];
+                                                 const SolverState* __restrict__ st, float2* __restrict__ W,
+                                                 float2* __restrict__ Wlo, int C, int Cp, int mode, int rank, int L) {
+  __shared__ double f[SMSM_MAX_C];
   __shared__ float2 As[CG_T][CG_T + 1];
-  __shared__ float2 Bs[CG_T][CG_T + 1];
+  __shared__ float2 Bh[CG_T][CG_T + 1], Bl[CG_T][CG_T + 1];
   const int l = blockIdx.z;  // flat (direction, slice)
   const float* s = eig + (size_t)l * Cp;
   const double eps = st[l / L].eps;
@@ -499,27 +464,48 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
       int rk = 0;
       const float sj = s[j];
       for (int k = 0; k < C; ++k) rk += (s[k] < sj) || (s[k] == sj && k < j);
-      f[j] = rk < C - rank ? 1.f : 0.f;
+      f[j] = rk < C - rank ? 1.0 : 0.0;
     } else {
-      f[j] = (float)(1.0 / sqrt(fmax((double)s[j], 0.0) + eps));
+      f[j] = 1.0 / sqrt(fmax((double)s[j], 0.0) + eps);
     }
   }
   __syncthreads();
   const float2* Vl = V + (size_t)l * C * C;
   const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
   const int a0 = blockIdx.y * CG_T, b0 = blockIdx.x * CG_T;
-  float2 acc = cmk(0.f, 0.f);
+  Df re{0.f, 0.f}, im{0.f, 0.f};
   for (int k0 = 0; k0 < C; k0 += CG_T) {
     const int ka = k0 + tx;
-    // As[row a][k] = V[a][k] f_k ; Bs[k][col b] = conj(V[b][k])  (loads coalesced along k)
-    As[ty][tx] = (a0 + ty < C && ka < C) ? cscale(Vl[(size_t)(a0 + ty) * C + ka], f[ka]) : cmk(0.f, 0.f);
-    Bs[tx][ty] = (b0 + ty < C && ka < C) ? conjf2(Vl[(size_t)(b0 + ty) * C + ka]) : cmk(0.f, 0.f);
+    // As[row a][k] = V[a][k];  B[k][col b] = f_k conj(V[b][k]) as hi + lo (loads coalesced along k)
+    As[ty][tx] = (a0 + ty < C && ka < C) ? Vl[(size_t)(a0 + ty) * C + ka] : cmk(0.f, 0.f);
+    float2 bh = cmk(0.f, 0.f), bl = cmk(0.f, 0.f);
+    if (b0 + ty < C && ka < C) {
+      const float2 v = Vl[(size_t)(b0 + ty) * C + ka];
+      const double br = f[ka] * (double)v.x, bi = -f[ka] * (double)v.y;
+      bh = cmk((float)br, (float)bi);
+      bl = cmk((float)(br - (double)bh.x), (float)(bi - (double)bh.y));
+    }
+    Bh[tx][ty] = bh;
+    Bl[tx][ty] = bl;
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
+#pragma unroll 4
+    for (int k = 0; k < CG_T; ++k) {
+      const float2 x = As[ty][k], y = Bh[k][tx], yl = Bl[k][tx];
+      df_add_prod(re, x.x, y.x);
+      df_add_prod(re, -x.y, y.y);
+      df_add_prod(im, x.x, y.y);
+      df_add_prod(im, x.y, y.x);
+      re.lo = fmaf(x.x, yl.x, fmaf(-x.y, yl.y, re.lo));
+      im.lo = fmaf(x.x, yl.y, fmaf(x.y, yl.x, im.lo));
+    }
     __syncthreads();
   }
-  if (a0 + ty < C && b0 + tx < C) W[((size_t)l * C + a0 + ty) * C + b0 + tx] = acc;
+  if (a0 + ty < C && b0 + tx < C) {
+    const size_t o = ((size_t)l * C + a0 + ty) * C + b0 + tx;
+    const float rh = re.hi + re.lo, ih = im.hi + im.lo;
+    W[o] = cmk(rh, ih);
+    Wlo[o] = cmk((re.hi - rh) + re.lo, (im.hi - ih) + im.lo);
+  }
 }
 
 static size_t jacobi_smem(int Cp) {
@@ -560,15 +546,16 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   if (T) T->begin(SMSM_STAGE_EIG);
   if (warm) {
     dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, nullptr, P->Gw, P->Gw3, C, 0);
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
     SMSM_LAUNCH_CHECK("k_congruence");
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw3, P->Gw2, nullptr, C, 1);
+    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw2, C, 1);
     SMSM_LAUNCH_CHECK("k_congruence");
   }
-  // rotation floor: a thousandth of eps_min relative to the largest diagonal entry (IRLS;
-  // eps_min = eps_min_rel * eps0_rel * s_max), 1e-9 of it for the fixed-rank projector
-  double frel = prm->mode == SMSM_MODE_NULLSPACE ? 1e-9 : 1e-3 * prm->eps0_rel * prm->eps_min_rel;
-  if (!(frel > 0.0)) frel = 1e-9;
+  // absolute floor of the rotation test, relative to the largest diagonal entry: far below
+  // every eigenvalue W resolves (the weight changes by about delta / (2 eps) for an
+  // off-diagonal entry delta left in place, so delta must stay many orders below eps_min);
+  // it only stops the churning of rounding noise between exactly zero eigenvalues
+  const double frel = 1e-12;
   k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->rotlog, P->sweeps, C, Cp,
                                                  msw, 1e-6f, (float)frel, P->st, P->L);
   SMSM_LAUNCH_CHECK("k_jacobi");
@@ -592,7 +579,7 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
                              prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
   dim3 gw((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
+  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->Wlo, C, Cp, prm->mode, prm->rank, P->L);
   SMSM_LAUNCH_CHECK("k_weights");
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;

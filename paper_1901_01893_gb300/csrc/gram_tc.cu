@@ -47,7 +47,7 @@
 
 #define GTC_PROD_WARPS 6                               // im2col producers
 #define GTC_THREADS (32 * (GTC_PROD_WARPS + 4 + 1))     // + 4 drain warps + 1 MMA warp
-#define GTC_EPOCH 16                                   // chunks accumulated in TMEM before a drain
+#define GTC_EPOCH 4                                    // chunks accumulated in TMEM before a drain
 #define GTC_MAXITER (1L << 22)
 
 // bounded wait that also gives up when another role has aborted

@@ -11,8 +11,12 @@
 // library image itself.
 //
 // Costs and limits:
-//  * Every GPU that loads the library holds SMSM_NOALLOC_SCRATCH_BYTES
-//    (8 MiB) for this array until the process exits.
+//  * Every GPU that loads the library's device code holds
+//    SMSM_NOALLOC_SCRATCH_BYTES (8 MiB) for this array until the process
+//    exits.  With lazy module loading (the CUDA default) the device code,
+//    and with it the array, is loaded on the first call of this entry point
+//    or the first launch of any kernel of the library on that device.
+//  * C = shots*filter^2 is at most 320.
 //  * A geometry whose partial sums need more than that is rejected with
 //    SMSM_ERR_ARG (the requirement is ceil((N-filter+1)/16) * C^2 * 16 bytes
 //    per slice, C = shots*filter^2; slices are processed one after another).
@@ -21,15 +25,15 @@
 //    wrong results; serialise them.  The kernels overwrite every scratch
 //    entry before reading it, so nothing needs clearing between calls and
 //    the array may hold any earlier call's contents.
-//  * The first call on each device looks the array's device address up
-//    (cudaGetSymbolAddress, with that device current).  Make that first call
-//    before any stream capture begins on the device.
-#include <mutex>
-
+//  * Every call looks the array's device address up (cudaGetSymbolAddress,
+//    with the caller's device current), so the address stays right after a
+//    context is torn down and created again (cudaDeviceReset), when the
+//    module may load at another address.  The first call on a device can
+//    load the library's device code; make it once at set-up, before any
+//    stream capture begins on that device.
 #include "common.cuh"
 
 #define SMSM_NOALLOC_SCRATCH_BYTES (8u << 20)
-#define SMSM_NOALLOC_MAX_DEVICES 64
 
 // The scratch array.  In host code this name is only a host-side stand-in,
 // never a device address: host code must use the pointer obtained below.
@@ -40,32 +44,19 @@ __global__ void k_gram_part(const float2* __restrict__ x, double2* __restrict__ 
                             int P1, int nkx, int tside, int periodic);
 __global__ void k_gram_reduce(const double2* __restrict__ part, double2* __restrict__ G, int L, int C, int nkx);
 
-static std::mutex g_scratch_mu;
-static double2* g_scratch_ptr[SMSM_NOALLOC_MAX_DEVICES];
-
+// Device address of the scratch array in the current context.  Looked up on every call
+// (a host-side table lookup in the runtime): no cached pointer can outlive a context.
 static smsm_status scratch_for_current_device(double2** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    smsm_set_error("smsm_hankel_gram_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_gram_scratch);
+  if (e != cudaSuccess || !p) {
+    int dev = -1;
+    cudaGetDevice(&dev);
+    smsm_set_error("smsm_hankel_gram_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
+                   cudaGetErrorString(e));
     return SMSM_ERR_CUDA;
   }
-  if (dev < 0 || dev >= SMSM_NOALLOC_MAX_DEVICES) {
-    smsm_set_error("smsm_hankel_gram_noalloc: device ordinal %d above %d", dev, SMSM_NOALLOC_MAX_DEVICES - 1);
-    return SMSM_ERR_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_gram_scratch);
-    if (e != cudaSuccess || !p) {
-      smsm_set_error("smsm_hankel_gram_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev,
-                     cudaGetErrorString(e));
-      return SMSM_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (double2*)p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = (double2*)p;
   return SMSM_OK;
 }
 
@@ -86,7 +77,11 @@ extern "C" smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, 
   const int P1 = N - r + 1;
   const int nkx = (P1 + 15) / 16;
   const size_t need = (size_t)nkx * C * C * sizeof(double2);
-  if (C > SMSM_MAX_C || need > SMSM_NOALLOC_SCRATCH_BYTES) {
+  if (C > SMSM_MAX_C) {
+    smsm_set_error("smsm_hankel_gram_noalloc: C = shots*filter^2 = %d is above %d", C, SMSM_MAX_C);
+    return SMSM_ERR_ARG;
+  }
+  if (need > SMSM_NOALLOC_SCRATCH_BYTES) {
     smsm_set_error("smsm_hankel_gram_noalloc: this geometry needs %zu bytes of scratch, above the fixed "
                    "%u bytes (C = shots*filter^2 = %d)", need, SMSM_NOALLOC_SCRATCH_BYTES, C);
     return SMSM_ERR_ARG;

@@ -371,10 +371,10 @@ class CNN:
         return loss.value if want_loss else None
 
 
-def learned_start(plan: "Plan", cnn: CNN, y: torch.Tensor, x: torch.Tensor | None = None) -> torch.Tensor:
-    """x = F(cnn(F^-1(A^H y))), the learned starting point of every problem of the plan."""
-    if x is None:
-        x = torch.empty(plan.x_shape, dtype=torch.complex64, device=y.device)
-    _check(lib().smsm_learned_start(plan._h, cnn._h, _dev(y, plan.y_shape, "y"), _dev(x, plan.x_shape, "x"),
-                                    _stream()))
-    return x
+def learned_start(plan: "Plan", cnn: CNN, x_in: torch.Tensor, x_out: torch.Tensor | None = None) -> torch.Tensor:
+    """x_out = F(cnn(F^-1(x_in))): the network applied to a k-space estimate of every problem."""
+    if x_out is None:
+        x_out = torch.empty(plan.x_shape, dtype=torch.complex64, device=x_in.device)
+    _check(lib().smsm_learned_start(plan._h, cnn._h, _dev(x_in, plan.x_shape, "x_in"),
+                                    _dev(x_out, plan.x_shape, "x_out"), _stream()))
+    return x_out

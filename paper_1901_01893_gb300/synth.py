@@ -25,6 +25,8 @@ Arrays are C-ordered with the x (readout, kx) index fastest.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 __all__ = ["CONFIGS", "make_group", "coords", "bandlimited_phase"]
@@ -78,16 +80,25 @@ def _poly_phase(rng: np.random.Generator, N: int) -> np.ndarray:
 def _field(rng: np.random.Generator, N: int, kmax: int = 3) -> np.ndarray:
     """Real field with spatial frequencies |k| <= kmax cycles per FOV, max |f| = pi."""
     u = coords(N)
-    X, Y = np.meshgrid(u, u, indexing="xy")
-    f = np.zeros((N, N), dtype=np.float64)
+    k = np.arange(-kmax, kmax + 1)
+    # one FOV is 2 units of u, so k cycles per FOV is exp(j*pi*k*u); the 2-D waves are
+    # products of 1-D ones, so the sum is E_y^T C E_x with the coefficients C on |k| <= kmax
+    E = np.exp(1j * np.pi * np.outer(k, u))  # [k][n]
+    Cf = np.zeros((2 * kmax + 1, 2 * kmax + 1), dtype=np.complex128)
     for ky in range(-kmax, kmax + 1):
         for kx in range(-kmax, kmax + 1):
             if kx * kx + ky * ky > kmax * kmax:
                 continue
-            c = rng.standard_normal() + 1j * rng.standard_normal()
-            # one FOV is 2 units of u, so k cycles per FOV is exp(j*pi*k*u)
-            f += np.real(c * np.exp(1j * np.pi * (kx * X + ky * Y)))
+            Cf[ky + kmax, kx + kmax] = rng.standard_normal() + 1j * rng.standard_normal()
+    f = np.real(E.T @ Cf @ E)  # f[y][x] = Re sum_{ky,kx} C exp(j pi (ky u_y + kx u_x))
     return f * (np.pi / np.max(np.abs(f)))
+
+
+@functools.lru_cache(maxsize=8)
+def _coils_cached(L: int, Nc: int, N: int) -> np.ndarray:
+    S = _coils(L, Nc, N)
+    S.setflags(write=False)
+    return S
 
 
 def _coils(L: int, Nc: int, N: int, ring: float = 1.2, sigma: float = 0.6,
@@ -128,7 +139,7 @@ def make_group(L: int, Ns: int, Nc: int, N: int, seed: int, field: bool = False,
             if field:
                 ph = ph + _field(rng, N)
             phase[l, i] = np.exp(1j * ph)
-    sens = _coils(L, Nc, N)
+    sens = _coils_cached(L, Nc, N).copy()  # the maps depend on the geometry only
     noise = (rng.standard_normal((Ns, Nc, N // Ns, N))
              + 1j * rng.standard_normal((Ns, Nc, N // Ns, N))) / np.sqrt(2.0)
     return dict(rho=rho, phase=phase, sens=sens, noise=noise)

@@ -9,7 +9,7 @@ product; the oracle is given those rounded values in FP64):
   * gradients of the batch's mean loss: NRMSE <= 1e-4 per layer for W and b (FP32
     accumulation over every pixel of the batch);
   * Adam steps on a fixed batch lower the loss, and the learned start is
-    x = F(cnn(F^-1(A^H y))) (checked against the oracle's operators).
+    x = F(cnn(F^-1(x_in))) (checked against the oracle's transforms and network).
 Sizes cover ragged 16-pixel tiles and channel blocks.
 """
 import numpy as np
@@ -125,6 +125,8 @@ def test_cnn_training_lowers_the_loss(smsm):
 
 
 def test_learned_start_is_the_cnn_between_the_transforms(smsm):
+    # x_in = A^H y made by the oracle; the expected value is the oracle's centred DFTs around
+    # the oracle's network, applied to the same input
     L, Ns, Nc, N, r = 2, 2, 4, 32, 3
     rng = np.random.default_rng(7)
     S = crandn(rng, L, Nc, N, N) / np.sqrt(Nc)
@@ -137,7 +139,8 @@ def test_learned_start_is_the_cnn_between_the_transforms(smsm):
     params = OC.init_params(rng, B, 8, 3, last_scale=1.0)
     v = flat(params)
     net.set_params(torch.from_numpy(v.astype(np.complex64)).to(DEV))
-    x = smsm.learned_start(plan, net, torch.from_numpy(y).to(DEV)).cpu().numpy()
-    a = O.ifft2c(O.adjoint(y.astype(np.complex128), S, L)).reshape(B, N, N)
+    xin = O.adjoint(y.astype(np.complex128), S, L)
+    x = smsm.learned_start(plan, net, torch.from_numpy(xin.astype(np.complex64)).to(DEV)).cpu().numpy()
+    a = O.ifft2c(xin.astype(np.complex64).astype(np.complex128)).reshape(B, N, N)
     ref = O.fft2c(OC.forward(a, unflat(bf16(v.astype(np.complex64)), shapes))).reshape(L, Ns, N, N)
     assert O.nrmse(x, ref) < 1e-5

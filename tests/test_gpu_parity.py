@@ -2,8 +2,9 @@
 
 Tolerances (NRMSE = ||gpu - oracle|| / ||oracle||):
   * FP32 operators (forward, adjoint, fft2c, Gram, filter penalty): 1e-5.
-  * the whole IRLS + CG solve, FP32 form: 1e-5 per slice (short schedules here;
-    the full schedules of the workloads are in test_gpu_solve_parity.py).
+  * the whole IRLS + CG solve, FP32 form: 2e-5 per slice (short schedules here;
+    the full schedules of the workloads, and how the FP32 operators' rounding grows
+    through CG into this bar, are in test_gpu_solve_parity.py).
   * reduced precision (BF16 split Gram): 1e-3, the metric's threshold.
 """
 import numpy as np
@@ -16,7 +17,7 @@ from paper_1901_01893_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
-SOLVE_TOL = 1e-5   # per slice, FP32 form
+SOLVE_TOL = 2e-5   # per slice, FP32 form
 BF16_TOL = 1e-3
 
 

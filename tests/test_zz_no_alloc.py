@@ -9,6 +9,8 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
+
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5  # the FP32-operator tolerance of the parity tests
@@ -44,7 +46,26 @@ def test_noalloc_gram_matches_planned_gram_twice(smsm, L, Ns, N, r):
         got = smsm.smsm_hankel_gram_noalloc(x, r)
         torch.cuda.synchronize()
         assert _nrmse(got, ref) < TOL, (call, _nrmse(got, ref))
+        if N <= 64:  # and against the FP64 oracle's Gram of the same (FP32) input
+            G = O.gram(x.cpu().numpy().astype(np.complex128), r)
+            assert O.nrmse(got.cpu().numpy(), G) < TOL
     plan.close()
+
+
+def test_noalloc_gram_allocates_nothing(smsm):
+    # after a first call (which may load the library's device code), further calls
+    # leave the device's free memory unchanged: the library allocates nothing
+    rng = np.random.default_rng(18)
+    x = _rand(rng, (2, 4, 64, 64))
+    G = torch.empty((2, 100, 100), dtype=torch.complex128, device="cuda:0")
+    smsm.smsm_hankel_gram_noalloc(x, 5, G=G)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        smsm.smsm_hankel_gram_noalloc(x, 5, G=G)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_gram_rejects_oversize_geometry(smsm):
@@ -54,3 +75,9 @@ def test_noalloc_gram_rejects_oversize_geometry(smsm):
         smsm.smsm_hankel_gram_noalloc(x, 6)
     assert e.value.status == smsm.SMSM_ERR_ARG
     assert "scratch" in str(e.value)
+    # the column limit has its own message
+    x = torch.zeros((1, 8, 64, 64), dtype=torch.complex64, device="cuda:0")
+    with pytest.raises(smsm.SmsmError) as e:
+        smsm.smsm_hankel_gram_noalloc(x, 7)  # C = 8 * 49 = 392 > 320
+    assert e.value.status == smsm.SMSM_ERR_ARG
+    assert "above 320" in str(e.value) and "scratch" not in str(e.value)
