@@ -71,13 +71,6 @@ static float2 expi_frac(long long num, long long den) {
   return make_float2((float)cos(a), (float)sin(a));
 }
 
-static double2 expi_frac64(long long num, long long den) {
-  long long r = num % den;
-  if (r < 0) r += den;
-  const double a = -2.0 * M_PI * (double)r / (double)den;
-  return make_double2(cos(a), sin(a));
-}
-
 template <typename T>
 static smsm_status dalloc(smsm_plan_s* P, T** p, size_t count) {
   const size_t bytes = count * sizeof(T);
@@ -101,7 +94,7 @@ static void free_plan(smsm_plan_s* P) {
   if (!P) return;
   void* ptrs[] = {P->twN,  P->twM,  P->tw_shot, P->cph,  P->Etab,  P->sensT, P->hA,   P->hB,
                   P->yh,   P->phaseT, P->xs,    P->bv,   P->rv,    P->pv,    P->qv,   P->ybuf,
-                  P->G64,  P->Gpart, P->eig,    P->rotlog, P->sweeps, P->V,   P->Wf,   P->Wlo, P->wper, P->Gw, P->Gw2,
+                  P->G64,  P->Gpart, P->eig,    P->sweeps, P->V,   P->Wf,   P->wper, P->Gw, P->Gw2,
                   P->wcls, P->multT, P->part_pq_col, P->part_pq_band, P->part_rr, P->st, P->rep,
                   P->Rpart, P->devflag, P->acorr, P->ash};
   for (void* p : ptrs)
@@ -234,11 +227,9 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(G64, LD * C * C);
   A(Gpart, LD * P->gram_nkx * C * C);
   A(eig, LD * Cp);
-  A(rotlog, LD * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2));
   A(sweeps, LD);
   A(V, LD * C * C);
   A(Wf, LD * C * C);
-  A(Wlo, LD * C * C);
   A(Gw, LD * C * C);
   A(Gw2, LD * C * C);
   A(wper, LD * shots * shots * R2 * R2);
@@ -305,10 +296,10 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
     st = upload(P->cph, h);
   }
   if (!st) {
-    // E[d][n] = exp(-j 2 pi (d - (r-1)) (n - N/2)/N), FP64
-    std::vector<double2> h((size_t)R2 * N);
+    // E[d][n] = exp(-j 2 pi (d - (r-1)) (n - N/2)/N)
+    std::vector<float2> h((size_t)R2 * N);
     for (int d = 0; d < R2; ++d)
-      for (int n = 0; n < N; ++n) h[(size_t)d * N + n] = expi_frac64((long long)(d - (r - 1)) * (n - N / 2), N);
+      for (int n = 0; n < N; ++n) h[(size_t)d * N + n] = expi_frac((long long)(d - (r - 1)) * (n - N / 2), N);
     st = upload(P->Etab, h);
   }
   if (!st && P->alias) {
@@ -472,8 +463,8 @@ extern "C" smsm_status smsm_apply_filters(smsm_plan_t plan, const void* W, const
   cudaStream_t s = S(stream);
   smsm_status st;
   const int B = plan->D * plan->L * plan->Ns;
-  if ((st = launch_w_from_c128(plan, (const double2*)W, plan->Wf, plan->Wlo, s))) return st;
-  if ((st = launch_filters(plan, plan->Wf, plan->Wlo, s))) return st;
+  if ((st = launch_w_from_c128(plan, (const double2*)W, plan->Wf, s))) return st;
+  if ((st = launch_filters(plan, plan->Wf, s))) return st;
   if ((st = launch_rowfft_out_T(plan, (const float2*)x, plan->hA, B, plan->N, 1, s))) return st;
   if ((st = launch_col(plan, COL_PEN, 0, plan->hA, plan->hB, nullptr, plan->multT, 1.f, nullptr, s))) return st;
   if ((st = launch_rowfft_in_T(plan, plan->hB, (float2*)out, B, plan->N, 0, s))) return st;

@@ -38,23 +38,6 @@ __device__ __forceinline__ void cfmacj(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
 
-// double-FP32 ("df32") accumulation: a value kept as hi + lo.  Adding an exact product
-// a*b = p + e (e = fma(a, b, -p)) with an error-free two-sum keeps about 44 bits, for
-// sums whose result is far smaller than their terms (FP64 runs at 1/64 of the FP32 rate
-// on this part).
-struct Df {
-  float hi, lo;
-};
-__device__ __forceinline__ void df_add_prod(Df& s, float a, float b) {
-  const float p = a * b;
-  const float e = fmaf(a, b, -p);
-  const float t = s.hi + p;
-  const float bb = t - s.hi;
-  const float err = (s.hi - (t - bb)) + (p - bb);
-  s.hi = t;
-  s.lo += err + e;
-}
-
 // asynchronous 8-byte global -> shared copy (completes at cp_async_wait_all)
 // Periodic penalty multiplier m_ii'[x][y] of one (direction, slice).  It is
 // Hermitian in the shot pair (wt_ii'[d] = conj(wt_i'i[-d]) because W is), so only
@@ -133,8 +116,7 @@ struct smsm_plan_s {
   FftDesc fN, fM;
   float sN;   // (-1)^(N/2)/sqrt(N)
   // tables (device)
-  float2 *twN, *twM, *tw_shot, *cph;
-  double2* Etab;     // [R2][N] exp(-j 2 pi (d-(r-1)) (n - N/2)/N) in FP64 (penalty multiplier)
+  float2 *twN, *twM, *tw_shot, *cph, *Etab;
   // coil maps, transposed [L][Nc][x][y]
   float2* sensT;
   int has_sens;
@@ -148,11 +130,10 @@ struct smsm_plan_s {
   double2* Gpart;    // [L][nkx][C][C]
   int gram_nkx;
   float* eig;        // [L][Cp]
-  float4* rotlog;    // [L][SMSM_MAX_SWEEPS][Cp-1][Cp/2]
   int* sweeps;       // [L]
-  float2 *V, *Wf, *Wlo;  // [LD][C][C]; W = Wf + Wlo (double-FP32: hi and its remainder)
+  float2 *V, *Wf;    // [LD][C][C]
   float2 *Gw, *Gw2;  // [LD][C][C] warm-start congruence V^H G V (and its half product)
-  double2* wper;     // [L][Ns][Ns][R2*R2] periodic filter taps, FP64
+  float2* wper;      // [L][Ns][Ns][R2*R2]
   float2* wcls;      // [LD][R2*R2 classes][Ns (i')][R2*R2 taps][Ns (i)] border correction taps
   float2* multT;     // [L][Ns(Ns+1)/2][N(x)][N(y)]: upper triangle of the Hermitian shot coupling
   double *part_pq_col, *part_pq_band, *part_rr;  // partial sums [D][PART]; part_rr: [2 banks][D][PART]
@@ -287,10 +268,10 @@ int gram_tc_cp(const smsm_plan_s* P);
 int gram_tc_nG(const smsm_plan_s* P);
 smsm_status gram_tc_init_attrs();
 smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
-smsm_status launch_filters(const smsm_plan_s* P, const float2* W, const float2* Wlo, cudaStream_t s);
+smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s);
 smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, float scale, double* dot_part,
                         cudaStream_t s);
-smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, float2* Wlo, cudaStream_t s);
+smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s);
 // eig.cu
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T);

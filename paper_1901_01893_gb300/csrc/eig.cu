@@ -6,12 +6,11 @@
 // Methods' choice of "the same rank for every slice").  The eigenvectors of
 // the annihilation relation's null space (Eq. 9) are the annihilating filters.
 //
-// Eigensolver: two-sided cyclic Jacobi for Hermitian matrices, one CTA per
-// slice, G held in shared memory, parallel round-robin ordering (C/2
-// disjoint rotations per round, all 2x2 blocks updated at once).  The
-// rotations of every round are logged, and a second kernel replays them on
-// the rows of V (independent rows, spread over many CTAs), so V never has to
-// share the CTA's shared memory with G.
+// Eigensolver: two-sided cyclic Jacobi for Hermitian matrices, G held in shared
+// memory, parallel round-robin ordering (C/2 disjoint rotations per round, all 2x2
+// blocks updated at once).  Each matrix takes a cluster of two CTAs: the second
+// holds V in its shared memory and applies every round's rotations to it while the
+// first goes on with the next round.
 //
 // Precision: the Gram arrives in FP64 and is rounded once to FP32 on load; rotations
 // are FP32.  What decides the accuracy of W is not the arithmetic width of the
@@ -31,6 +30,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "umma.cuh"
 
 #define CG_T 16  // tile edge of the small complex GEMMs (weights, warm-start congruence)
 
@@ -85,21 +85,194 @@ __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, 
   }
 }
 
-__global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, const float2* __restrict__ Gw,
-                                                 float* __restrict__ eig, float4* __restrict__ rlog,
-                                                 int* __restrict__ sweeps_out, int C, int Cp, int max_sweeps,
-                                                 float tol, float floor_rel, SolverState* st, int L) {
-  extern __shared__ float2 g[];
+// The eigen step runs as a cluster of two CTAs per matrix.  Rank 0 holds G and runs
+// the Jacobi rounds; rank 1 holds V (the previous eigenvectors, or I) and applies
+// each round's rotations to it as they come, so V never leaves the chip and no log
+// of rotations is written.  Rank 0 sends round m's rotations into rank 1's shared
+// memory (buffer m & 1) and arrives on rank 1's `full` mbarrier; rank 1 applies them
+// and arrives on rank 0's `empty` mbarrier, which rank 0 waits for before it reuses
+// the buffer.  A message with header -1 ends the exchange.  Every wait is bounded:
+// on a timeout the waiting side raises the device error flag (SMSM_ERR_TIMEOUT) and
+// goes on, and both CTAs meet at a final cluster barrier, so neither leaves while the
+// other may still touch its shared memory.
+#define JAC_MAXWAIT (1L << 22)
+#define JAC_VS 3  // pair slots per lane of the V-CTA: Cp/2 <= 32 JAC_VS (Cp <= 192)
+
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cl_st_v4(uint32_t a, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void cl_st_s32(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cl_arrive(uint32_t remote_mbar, uint32_t count) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(remote_mbar), "r"(count)
+               : "memory");
+}
+// bounded wait on a local mbarrier phase, acquiring what the other CTA released
+__device__ __forceinline__ bool cl_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+  for (long it = 0; it < JAC_MAXWAIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        "selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// shared-memory layout (bytes), the same in both CTAs: region A holds G (rank 0) or V
+// (rank 1), both with row stride Cp + 1; region B holds rank 0's rotation, p and q
+// tables or rank 1's two message buffers of Cp/2 rotations.
+__host__ __device__ inline size_t jac_region_a(int Cp) { return (((size_t)Cp * (Cp + 1) * 8) + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t jac_smem_bytes(int Cp) { return jac_region_a(Cp) + (size_t)(Cp / 2) * 32; }
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
+    k_jacobi(const double2* __restrict__ G, const float2* __restrict__ Gw, float* __restrict__ eig,
+             float2* __restrict__ V, int warmv, int* __restrict__ sweeps_out, int C, int Cp, int max_sweeps, float tol,
+             float floor_rel, SolverState* st, int L, int* __restrict__ errflag) {
+  extern __shared__ __align__(16) unsigned char jsm[];
+  __shared__ __align__(8) uint64_t full_b[2], empty_b[2];
+  __shared__ int hdr[2];
+  __shared__ float dmax;
+  const uint32_t rank = cl_rank();
+  const int l = blockIdx.x >> 1, tid = threadIdx.x, nt = blockDim.x;
   const int ld = Cp + 1;
   const int half = Cp / 2;
+  float2* g = reinterpret_cast<float2*>(jsm);                          // rank 0: G;  rank 1: V
+  unsigned char* regb = jsm + jac_region_a(Cp);
+  float4* rbuf = reinterpret_cast<float4*>(regb);                      // rank 1: [2][half]
+  if (tid == 0) {
+    mbar_init(&full_b[0], (uint32_t)half);
+    mbar_init(&full_b[1], (uint32_t)half);
+    mbar_init(&empty_b[0], 1);
+    mbar_init(&empty_b[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  cl_sync();  // every mbarrier is initialised before the other CTA may arrive on it
+
+  if (rank == 1) {
+    // ---------------- V: apply every round's rotations as they arrive ----------------
+    float2* Vl = V + (size_t)l * C * C;
+    for (int e = tid; e < C * Cp; e += nt) {
+      const int t = e / Cp, j = e - t * Cp;
+      float2 v = cmk(0.f, 0.f);
+      if (j < C) v = warmv ? Vl[(size_t)t * C + j] : cmk(j == t ? 1.f : 0.f, 0.f);
+      g[t * ld + j] = v;
+    }
+    __syncthreads();
+    // lane j applies the pairs k = j + 32 u of every round to the rows t = warp + 32 v;
+    // the pairs' round-robin indices advance by one (mod Cp - 1) from round to round
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const int mm = Cp - 1;
+    int ia[JAC_VS], ib[JAC_VS];
+    bool ok = true;
+    int last = -1;
+    for (long m = 0;; ++m) {
+      const int b = (int)(m & 1);
+      if (ok && !cl_wait(&full_b[b], (uint32_t)((m >> 1) & 1))) {
+        ok = false;
+        if (tid == 0) atomicExch(errflag, SMSM_ERR_TIMEOUT);
+      }
+      if (!__syncthreads_and(ok)) break;
+      const int round = hdr[b];
+      if (round < 0) break;
+#pragma unroll
+      for (int u = 0; u < JAC_VS; ++u) {
+        const int k = lane + 32 * u;
+        if (round == 0 || round != last + 1) {  // a new sweep starts over from round 0
+          ia[u] = (k + round) % mm;
+          ib[u] = (mm - k % mm + round) % mm;
+        } else {
+          ia[u] = ia[u] + 1 == mm ? 0 : ia[u] + 1;
+          ib[u] = ib[u] + 1 == mm ? 0 : ib[u] + 1;
+        }
+      }
+      last = round;
+      const float4* R = rbuf + b * half;
+#pragma unroll
+      for (int u = 0; u < JAC_VS; ++u) {
+        const int k = lane + 32 * u;
+        if (k >= half) continue;
+        const float4 J = R[k];
+        if (is_ident(J)) continue;
+        int pa, pb;
+        if (k == 0) {
+          pa = 0;
+          pb = 1 + round;
+        } else {
+          pa = 1 + ia[u];
+          pb = 1 + ib[u];
+        }
+        const int p = min(pa, pb), q = max(pa, pb);
+        const float2 e = cmk(J.z, J.w);
+        for (int t = warp; t < C; t += nw) {
+          float2* row = g + t * ld;
+          const float2 vp = row[p], evq = cmul(e, row[q]);
+          row[p] = cmk(J.x * vp.x - J.y * evq.x, J.x * vp.y - J.y * evq.y);
+          row[q] = cmk(J.y * vp.x + J.x * evq.x, J.y * vp.y + J.x * evq.y);
+        }
+      }
+      __syncthreads();  // every thread is done with buffer b (and with this round's rows)
+      if (tid == 0) cl_arrive(cl_map(&empty_b[b], 0), 1);
+    }
+    __syncthreads();
+    for (int e = tid; e < C * C; e += nt) {
+      const int t = e / C, j = e - t * C;
+      Vl[e] = g[t * ld + j];
+    }
+    __syncthreads();
+    cl_sync();  // rank 0 has sent its last message: nothing touches this CTA any more
+    return;
+  }
+
+  // ---------------- rank 0: Jacobi rounds on G ----------------
   const int nh = (half + 1) & ~1;  // triangle edge rounded up to even (virtual pair skipped)
   const int nblk = (nh / 2) * (nh + 1);
   const float inv_n1 = 1.f / (float)(nh + 1);
-  float4* rot = reinterpret_cast<float4*>(g + (size_t)Cp * ld + ((Cp * ld) & 1));
+  float4* rot = reinterpret_cast<float4*>(regb);
   int* rp = reinterpret_cast<int*>(rot + half);
   int* rq = rp + half;
-  __shared__ float dmax;
-  const int l = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t r_buf = cl_map(rbuf, 1), r_hdr = cl_map(hdr, 1);
+  const uint32_t r_full0 = cl_map(&full_b[0], 1), r_full1 = cl_map(&full_b[1], 1);
+  long msg = 0;  // messages sent to rank 1
+  bool link = true;
+  // send round `round` (or -1: the end) from the rotation table; the writers of a message
+  // are the threads tid < half (each arrives once), the end message is thread 0's alone
+  auto send = [&](int round) {
+    const int b = (int)(msg & 1);
+    if (msg >= 2 && link && !cl_wait(&empty_b[b], (uint32_t)(((msg >> 1) - 1) & 1))) {
+      link = false;
+      atomicExch(errflag, SMSM_ERR_TIMEOUT);
+    }
+    if (round >= 0) {
+      cl_st_v4(r_buf + (uint32_t)((b * half + tid) * sizeof(float4)), rot[tid]);
+      if (tid == 0) cl_st_s32(r_hdr + (uint32_t)(b * sizeof(int)), round);
+      cl_arrive(b ? r_full1 : r_full0, 1);
+    } else {
+      cl_st_s32(r_hdr + (uint32_t)(b * sizeof(int)), -1);
+      cl_arrive(b ? r_full1 : r_full0, (uint32_t)half);
+    }
+    ++msg;
+  };
   const double2* Gl = G + (size_t)l * C * C;
   const float2* Gwl = Gw ? Gw + (size_t)l * C * C : nullptr;
   for (int e = tid; e < Cp * Cp; e += nt) {
@@ -155,7 +328,9 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
           rotated = 1;
         }
         rot[tid] = J;
-        rlog[(((size_t)l * SMSM_MAX_SWEEPS + sw) * (Cp - 1) + round) * half + tid] = J;
+        send(round);
+      } else {
+        ++msg;  // every thread counts the messages (only the writers use the count)
       }
       __syncthreads();
 #pragma unroll
@@ -234,108 +409,10 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double2* __restrict__ G, 
   if (pending && tid == 0 && st) atomicCAS(&st[l / L].status, 0, (int)SMSM_ERR_EIG_UNCONVERGED);
   for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
-}
-
-// V = V0 * (product of the logged rotations), V0 = I or the previous V (warm).
-// One CTA per (matrix, VA_WARPS VA_ROWS_PER_WARP rows); each warp owns VA_ROWS_PER_WARP
-// rows in shared memory and applies every round's rotations to them.  Lane j
-// handles the pairs k = j + 32 u; their indices advance by one (mod Cp-1) from
-// round to round, and the next round's rotations are loaded while the current
-// ones are applied.
-#define VA_ROWS_PER_WARP 4
-#define VA_WARPS 12  // 48 rows per CTA: three CTAs cover the 144 rows of the common C = 144
-#define VA_SLOTS 3   // pair slots per lane: Cp/2 <= 32 VA_SLOTS (Cp <= 192)
-__global__ void __launch_bounds__(32 * VA_WARPS) k_vapply(const float4* __restrict__ rlog, const int* __restrict__ sweeps,
-                                                float2* __restrict__ V, int C, int Cp, int warm) {
-  extern __shared__ float2 rows[];
-  const int l = blockIdx.x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t0 = (blockIdx.y * VA_WARPS + w) * VA_ROWS_PER_WARP;
-  float2* myrows = rows + (size_t)w * VA_ROWS_PER_WARP * Cp;
-  float2* Vl = V + (size_t)l * C * C;
-#pragma unroll
-  for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
-    const int t = t0 + rr;
-    for (int j = lane; j < Cp; j += 32) {
-      float2 v = cmk(0.f, 0.f);
-      if (t < C && j < C) v = warm ? Vl[(size_t)t * C + j] : cmk(j == t ? 1.f : 0.f, 0.f);
-      myrows[rr * Cp + j] = v;
-    }
-  }
-  __syncwarp();
-  const int nsw = sweeps[l];
-  const int half = Cp / 2, m = Cp - 1;
-  const int nround = nsw * m;
-  const float4* lg0 = rlog + (size_t)l * SMSM_MAX_SWEEPS * m * half;
-  // round-robin state of slot u (pair k = lane + 32u): jpair with ia = (k + round) % m,
-  // ib = (m - k + round) % m, advanced by one each round
-  int ia[VA_SLOTS], ib[VA_SLOTS];
-#pragma unroll
-  for (int u = 0; u < VA_SLOTS; ++u) {
-    const int k = lane + 32 * u;
-    ia[u] = k % m;
-    ib[u] = (m - k % m) % m;
-  }
-  float4 Jn[VA_SLOTS];
-#pragma unroll
-  for (int u = 0; u < VA_SLOTS; ++u) {
-    const int k = lane + 32 * u;
-    Jn[u] = (k < half && nround > 0) ? __ldg(lg0 + k) : make_float4(1.f, 0.f, 1.f, 0.f);
-  }
-  for (int gr = 0; gr < nround; ++gr) {
-    const int round = gr % m;  // rounds of a sweep are logged contiguously, sweeps follow each other
-    if (round == 0) {
-#pragma unroll
-      for (int u = 0; u < VA_SLOTS; ++u) {
-        const int k = lane + 32 * u;
-        ia[u] = k % m;
-        ib[u] = (m - k % m) % m;
-      }
-    }
-    float4 J[VA_SLOTS];
-#pragma unroll
-    for (int u = 0; u < VA_SLOTS; ++u) J[u] = Jn[u];
-    if (gr + 1 < nround) {
-      const float4* lg = lg0 + (size_t)(gr + 1) * half;
-#pragma unroll
-      for (int u = 0; u < VA_SLOTS; ++u) {
-        const int k = lane + 32 * u;
-        if (k < half) Jn[u] = __ldg(lg + k);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < VA_SLOTS; ++u) {
-      const int k = lane + 32 * u;
-      if (k < half && !is_ident(J[u])) {
-        int a, b;
-        if (k == 0) {
-          a = 0;
-          b = 1 + round;
-        } else {
-          a = 1 + ia[u];
-          b = 1 + ib[u];
-        }
-        const int p = min(a, b), q = max(a, b);
-        const float2 e = cmk(J[u].z, J[u].w);
-#pragma unroll
-        for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
-          float2* row = myrows + rr * Cp;
-          const float2 vp = row[p], evq = cmul(e, row[q]);
-          row[p] = cmk(J[u].x * vp.x - J[u].y * evq.x, J[u].x * vp.y - J[u].y * evq.y);
-          row[q] = cmk(J[u].y * vp.x + J[u].x * evq.x, J[u].y * vp.y + J[u].x * evq.y);
-        }
-      }
-      ia[u] = ia[u] + 1 == m ? 0 : ia[u] + 1;
-      ib[u] = ib[u] + 1 == m ? 0 : ib[u] + 1;
-    }
-    __syncwarp();
-  }
-#pragma unroll
-  for (int rr = 0; rr < VA_ROWS_PER_WARP; ++rr) {
-    const int t = t0 + rr;
-    if (t >= C) continue;
-    for (int j = lane; j < C; j += 32) Vl[(size_t)t * C + j] = myrows[rr * Cp + j];
-  }
+  __syncthreads();  // rank 1 reads the last rounds' buffers until it sees the end message
+  if (tid == 0) send(-1);
+  __syncthreads();
+  cl_sync();
 }
 
 // Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
@@ -446,16 +523,12 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
 
 // W[a][b] = sum_j V[a][j] f_j conj(V[b][j]), f_j = (max(s_j, 0) + eps)^(-1/2) (IRLS) or
 // [s_j among the C - rank smallest] (NULLSPACE).  16 x 16 output tiles, K tiles of 16.
-// The weights span up to sqrt(s_max / eps_min), and W's entries carry the largest of
-// them while the penalty needs W's action on the directions of the smallest: so the sum
-// is accumulated in double-FP32 (f_j conj(V[b][j]) formed in FP64 and split into hi + lo,
-// the products with V[a][j] taken exactly) and W is returned as hi (Wf) + lo (Wlo).
 __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, const float* __restrict__ eig,
-                                                 const SolverState* __restrict__ st, float2* __restrict__ W,
-                                                 float2* __restrict__ Wlo, int C, int Cp, int mode, int rank, int L) {
-  __shared__ double f[SMSM_MAX_C];
+                                                 const SolverState* __restrict__ st, float2* __restrict__ W, int C,
+                                                 int Cp, int mode, int rank, int L) {
+  __shared__ float f[SMSM_MAX_C];
   __shared__ float2 As[CG_T][CG_T + 1];
-  __shared__ float2 Bh[CG_T][CG_T + 1], Bl[CG_T][CG_T + 1];
+  __shared__ float2 Bs[CG_T][CG_T + 1];
   const int l = blockIdx.z;  // flat (direction, slice)
   const float* s = eig + (size_t)l * Cp;
   const double eps = st[l / L].eps;
@@ -464,54 +537,29 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
       int rk = 0;
       const float sj = s[j];
       for (int k = 0; k < C; ++k) rk += (s[k] < sj) || (s[k] == sj && k < j);
-      f[j] = rk < C - rank ? 1.0 : 0.0;
+      f[j] = rk < C - rank ? 1.f : 0.f;
     } else {
-      f[j] = 1.0 / sqrt(fmax((double)s[j], 0.0) + eps);
+      f[j] = (float)(1.0 / sqrt(fmax((double)s[j], 0.0) + eps));
     }
   }
   __syncthreads();
   const float2* Vl = V + (size_t)l * C * C;
   const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
   const int a0 = blockIdx.y * CG_T, b0 = blockIdx.x * CG_T;
-  Df re{0.f, 0.f}, im{0.f, 0.f};
+  float2 acc = cmk(0.f, 0.f);
   for (int k0 = 0; k0 < C; k0 += CG_T) {
     const int ka = k0 + tx;
-    // As[row a][k] = V[a][k];  B[k][col b] = f_k conj(V[b][k]) as hi + lo (loads coalesced along k)
-    As[ty][tx] = (a0 + ty < C && ka < C) ? Vl[(size_t)(a0 + ty) * C + ka] : cmk(0.f, 0.f);
-    float2 bh = cmk(0.f, 0.f), bl = cmk(0.f, 0.f);
-    if (b0 + ty < C && ka < C) {
-      const float2 v = Vl[(size_t)(b0 + ty) * C + ka];
-      const double br = f[ka] * (double)v.x, bi = -f[ka] * (double)v.y;
-      bh = cmk((float)br, (float)bi);
-      bl = cmk((float)(br - (double)bh.x), (float)(bi - (double)bh.y));
-    }
-    Bh[tx][ty] = bh;
-    Bl[tx][ty] = bl;
+    // As[row a][k] = V[a][k] f_k ; Bs[k][col b] = conj(V[b][k])  (loads coalesced along k)
+    As[ty][tx] = (a0 + ty < C && ka < C) ? cscale(Vl[(size_t)(a0 + ty) * C + ka], f[ka]) : cmk(0.f, 0.f);
+    Bs[tx][ty] = (b0 + ty < C && ka < C) ? conjf2(Vl[(size_t)(b0 + ty) * C + ka]) : cmk(0.f, 0.f);
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < CG_T; ++k) {
-      const float2 x = As[ty][k], y = Bh[k][tx], yl = Bl[k][tx];
-      df_add_prod(re, x.x, y.x);
-      df_add_prod(re, -x.y, y.y);
-      df_add_prod(im, x.x, y.y);
-      df_add_prod(im, x.y, y.x);
-      re.lo = fmaf(x.x, yl.x, fmaf(-x.y, yl.y, re.lo));
-      im.lo = fmaf(x.x, yl.y, fmaf(x.y, yl.x, im.lo));
-    }
+#pragma unroll
+    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
     __syncthreads();
   }
-  if (a0 + ty < C && b0 + tx < C) {
-    const size_t o = ((size_t)l * C + a0 + ty) * C + b0 + tx;
-    const float rh = re.hi + re.lo, ih = im.hi + im.lo;
-    W[o] = cmk(rh, ih);
-    Wlo[o] = cmk((re.hi - rh) + re.lo, (im.hi - ih) + im.lo);
-  }
+  if (a0 + ty < C && b0 + tx < C) W[((size_t)l * C + a0 + ty) * C + b0 + tx] = acc;
 }
 
-static size_t jacobi_smem(int Cp) {
-  const size_t gsz = (size_t)Cp * (Cp + 1) + (((size_t)Cp * (Cp + 1)) & 1);  // float2, keep 16-byte alignment
-  return gsz * sizeof(float2) + (size_t)(Cp / 2) * (sizeof(float4) + 2 * sizeof(int));
-}
 
 smsm_status eig_init_attrs(int Cp) {
   const int nh = (Cp / 2 + 1) & ~1;
@@ -519,22 +567,16 @@ smsm_status eig_init_attrs(int Cp) {
     smsm_set_error("Jacobi kernel: C = %d is above its block schedule's limit", Cp);
     return SMSM_ERR_ARG;
   }
-  size_t sm = jacobi_smem(Cp);
+  const size_t sm = jac_smem_bytes(Cp);
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) {
     smsm_set_error("Jacobi kernel cannot get %zu bytes of shared memory: %s", sm, cudaGetErrorString(e));
     return SMSM_ERR_ARG;
   }
-  const size_t vsm = (size_t)VA_WARPS * VA_ROWS_PER_WARP * Cp * sizeof(float2);
-  e = cudaFuncSetAttribute(k_vapply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
-  if (e != cudaSuccess) {
-    smsm_set_error("rotation replay kernel cannot get %zu bytes of shared memory: %s", vsm, cudaGetErrorString(e));
-    return SMSM_ERR_ARG;
-  }
   return SMSM_OK;
 }
 
-size_t eig_jacobi_smem(int Cp) { return jacobi_smem(Cp); }
+size_t eig_jacobi_smem(int Cp) { return jac_smem_bytes(Cp); }
 
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T) {
@@ -556,15 +598,12 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   // off-diagonal entry delta left in place, so delta must stay many orders below eps_min);
   // it only stops the churning of rounding noise between exactly zero eigenvalues
   const double frel = 1e-12;
-  k_jacobi<<<P->LD, 1024, jacobi_smem(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->rotlog, P->sweeps, C, Cp,
-                                                 msw, 1e-6f, (float)frel, P->st, P->L);
+  // two CTAs per matrix: the Jacobi rounds on G and, beside them, V times every rotation
+  k_jacobi<<<2 * P->LD, 1024, jac_smem_bytes(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->V, warm, P->sweeps, C,
+                                                        Cp, msw, 1e-6f, (float)frel, P->st, P->L, P->devflag);
   SMSM_LAUNCH_CHECK("k_jacobi");
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  dim3 gv(P->LD, (C + VA_WARPS * VA_ROWS_PER_WARP - 1) / (VA_WARPS * VA_ROWS_PER_WARP));
-  k_vapply<<<gv, 32 * VA_WARPS, (size_t)VA_WARPS * VA_ROWS_PER_WARP * Cp * sizeof(float2), s>>>(P->rotlog, P->sweeps, P->V, C, Cp,
-                                                                              warm);
-  SMSM_LAUNCH_CHECK("k_vapply");
   {
     dim3 gn((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
     k_ns<<<gn, CG_T * CG_T, 0, s>>>(P->V, nullptr, P->Gw, C, 0);
@@ -579,7 +618,7 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
                              prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
   dim3 gw((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, P->Wlo, C, Cp, prm->mode, prm->rank, P->L);
+  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
   SMSM_LAUNCH_CHECK("k_weights");
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;

@@ -47,7 +47,6 @@
 
 #define GTC_PROD_WARPS 6                               // im2col producers
 #define GTC_THREADS (32 * (GTC_PROD_WARPS + 4 + 1))     // + 4 drain warps + 1 MMA warp
-#define GTC_EPOCH 4                                    // chunks accumulated in TMEM before a drain
 #define GTC_MAXITER (1L << 22)
 
 // bounded wait that also gives up when another role has aborted
@@ -80,6 +79,11 @@ struct GtcLayout {
 // Operand pieces and MMA k-steps (32 bytes of K each) per staged chunk of each form.
 __host__ __device__ constexpr int gtc_planes(int prec) { return prec == 2 ? 3 : 2; }
 __host__ __device__ constexpr int gtc_ksteps(int prec) { return prec == 2 ? 1 : 2; }
+// Chunks accumulated in TMEM before a drain into the FP32 partial.  Every MMA rounds the
+// accumulator once, so the epoch bounds the accumulation error: 4 chunks (24 roundings)
+// keep the FP32 form's Gram at FP32-FMA accuracy (5e-8 rms of sqrt(G_ii G_jj), measured;
+// 16 chunks gave 4e-7); the BF16 split form's own 2^-16 products allow 16.
+__host__ __device__ constexpr int gtc_epoch(int prec) { return prec == 2 ? 4 : 16; }
 
 __host__ __device__ inline GtcLayout gtc_layout(int Ns, int N, int r, int Cp, int periodic, int prec) {
   GtcLayout L;
@@ -119,6 +123,7 @@ __global__ void __launch_bounds__(GTC_THREADS, 1)
   constexpr int KSTEP = gtc_ksteps(PREC);        // MMA k-steps per staged chunk
   constexpr int NPL = gtc_planes(PREC);          // operand pieces per chunk
   constexpr int KQ = 2 * KSTEP;                  // core matrices along K per chunk
+  constexpr int GTC_EPOCH = gtc_epoch(PREC);     // chunks accumulated in TMEM before a drain
   constexpr int KCH = KQ * EPC;                  // patches per chunk
   constexpr uint32_t LBO = 128;                  // next core matrix along K
   constexpr uint32_t SBO = 128 * KQ;             // next 8-row group

@@ -166,24 +166,14 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
 // accumulating rows from the top (prefix classes) or from the bottom (suffix
 // classes) and, within the rows accumulated so far, column prefix and suffix
 // sums gives each class sum as one lookup.  The periodic filter is the full sum.
-// The sums run in FP64 over W = hi + lo (hi staged in shared memory, lo read from
-// global memory): the taps are differences of large entries of W wherever its weights
-// span a wide range, and the periodic taps feed the multiplier in FP64.
 #define FILT_MAXR 12
-__device__ __forceinline__ double2 filt_a(const float2* wi, const float2* __restrict__ wlo, int ldw, int C, int r,
-                                          int dy, int dx, int py, int px) {
+__device__ __forceinline__ float2 filt_a(const float2* wi, int ldw, int r, int dy, int dx, int py, int px) {
   const int qy = py + dy, qx = px + dx;
-  if (qy < 0 || qy >= r || qx < 0 || qx >= r) return make_double2(0.0, 0.0);
-  const float2 h = wi[(qy * r + qx) * ldw + py * r + px];
-  const float2 l = wlo[(size_t)(qy * r + qx) * C + py * r + px];
-  return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+  return (qy >= 0 && qy < r && qx >= 0 && qx < r) ? wi[(qy * r + qx) * ldw + py * r + px] : cmk(0.f, 0.f);
 }
-__device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 dround(double2 a) { return cmk((float)a.x, (float)a.y); }
 
-__global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, const float2* __restrict__ Wlo,
-                                                 float2* __restrict__ dcls, double2* __restrict__ wper, int Ns, int r,
-                                                 int C, int classes) {
+__global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, float2* __restrict__ dcls,
+                                                 float2* __restrict__ wper, int Ns, int r, int C, int classes) {
   extern __shared__ float2 sW[];  // [r*r (q)][C + 1]
   const int R2 = 2 * r - 1, RR = R2 * R2;
   const int j = blockIdx.x;
@@ -191,7 +181,6 @@ __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, c
   const int rr = r * r;
   const int ldw = C + 1;
   const float2* Wl = W + (size_t)l * C * C + (size_t)j * rr * C;
-  const float2* Wll = Wlo + (size_t)l * C * C + (size_t)j * rr * C;
   for (int e = threadIdx.x; e < rr * C; e += blockDim.x) {
     const int q = e / C, c = e - q * C;
     sW[q * ldw + c] = Wl[e];
@@ -201,35 +190,34 @@ __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, c
     const int i = t % Ns, d = t / Ns;
     const int dy = d / R2 - (r - 1), dx = d % R2 - (r - 1);
     const float2* wi = sW + i * rr;
-    const float2* wli = Wll + i * rr;
     // periodic filter: the sum over every p
-    double2 sp = make_double2(0.0, 0.0);
+    float2 sp = cmk(0.f, 0.f);
     for (int py = 0; py < r; ++py)
-      for (int px = 0; px < r; ++px) sp = dadd(sp, filt_a(wi, wli, ldw, C, r, dy, dx, py, px));
+      for (int px = 0; px < r; ++px) sp = cadd(sp, filt_a(wi, ldw, r, dy, dx, py, px));
     wper[((size_t)(l * Ns + i) * Ns + j) * RR + d] = sp;
     if (!classes) continue;  // periodic patches: no border band, no class taps
     float2* out = dcls + ((size_t)l * RR * Ns + j) * RR * Ns + (size_t)d * Ns + i;  // + cls * Ns * RR * Ns
     const size_t cstride = (size_t)Ns * RR * Ns;
     // pass 0: rows 0..cy (classes cy <= r-1); pass 1: rows cy-r+1..r-1 (classes cy >= r-1)
     for (int pass = 0; pass < 2; ++pass) {
-      double2 cpre[FILT_MAXR], csuf[FILT_MAXR];  // column prefix / suffix sums over the rows so far
+      float2 cpre[FILT_MAXR], csuf[FILT_MAXR];  // column prefix / suffix sums over the rows so far
 #pragma unroll
-      for (int k = 0; k < FILT_MAXR; ++k) cpre[k] = csuf[k] = make_double2(0.0, 0.0);
+      for (int k = 0; k < FILT_MAXR; ++k) cpre[k] = csuf[k] = cmk(0.f, 0.f);
       for (int step = 0; step < r; ++step) {
         const int py = pass == 0 ? step : r - 1 - step;
-        double2 run = make_double2(0.0, 0.0);
+        float2 run = cmk(0.f, 0.f);
 #pragma unroll
         for (int px = 0; px < FILT_MAXR; ++px)
           if (px < r) {
-            run = dadd(run, filt_a(wi, wli, ldw, C, r, dy, dx, py, px));
-            cpre[px] = dadd(cpre[px], run);
+            run = cadd(run, filt_a(wi, ldw, r, dy, dx, py, px));
+            cpre[px] = cadd(cpre[px], run);
           }
-        run = make_double2(0.0, 0.0);
+        run = cmk(0.f, 0.f);
 #pragma unroll
         for (int k = FILT_MAXR - 1; k >= 0; --k)
           if (k < r) {
-            run = dadd(run, filt_a(wi, wli, ldw, C, r, dy, dx, py, k));
-            csuf[k] = dadd(csuf[k], run);
+            run = cadd(run, filt_a(wi, ldw, r, dy, dx, py, k));
+            csuf[k] = cadd(csuf[k], run);
           }
         // rows so far: [0, step] (pass 0: class cy = step) or [r-1-step, r-1] (pass 1:
         // class cy = 2r-2-step, whose valid rows are [cy-r+1, r-1])
@@ -240,10 +228,9 @@ __global__ void __launch_bounds__(256) k_filters(const float2* __restrict__ W, c
         for (int cx = 0; cx < 2 * FILT_MAXR - 1; ++cx)
           if (cx < R2) {
             // columns [0, cx] (cx <= r-1) or [cx-r+1, r-1] (cx >= r-1)
-            const double2 sc = cx <= r - 1 ? cpre[cx < FILT_MAXR ? cx : 0] : csuf[cx - r + 1 < FILT_MAXR ? cx - r + 1 : 0];
+            const float2 sc = cx <= r - 1 ? cpre[cx < FILT_MAXR ? cx : 0] : csuf[cx - r + 1 < FILT_MAXR ? cx - r + 1 : 0];
             const bool inx = (cx < r - 1) ? (dx >= -cx) : (cx > r - 1 ? dx <= 2 * r - 2 - cx : true);
-            out[(size_t)(cy * R2 + cx) * cstride] =
-                (iny && inx) ? dround(make_double2(sc.x - sp.x, sc.y - sp.y)) : dround(make_double2(-sp.x, -sp.y));
+            out[(size_t)(cy * R2 + cx) * cstride] = (iny && inx) ? csub(sc, sp) : cscale(sp, -1.f);
           }
       }
     }
@@ -254,17 +241,12 @@ static size_t filters_smem(const smsm_plan_s* P) { return (size_t)P->r * P->r * 
 
 // multT[l][pk(i,i')][x][y] = sum_dy E[dy][y] sum_dx wt_ii'[dy][dx] E[dx][x],  E[d][n] = exp(-j 2 pi (d-(r-1)) (n - N/2)/N),
 // for i <= i' only (the multiplier is Hermitian in the shot pair); the diagonal planes are real.
-// The multiplier is small wherever the image lies (there the annihilating filters vanish)
-// and its taps are large, so both sums are extended: the first (over dx, a few columns per
-// CTA) in FP64, the second (over dy, every pixel) in double-FP32 with E and the partial
-// sums as hi + lo; each value is rounded once to FP32 at the end.
 #define MULT_XB 8
-__global__ void __launch_bounds__(256) k_mult(const double2* __restrict__ wper, const double2* __restrict__ E,
+__global__ void __launch_bounds__(256) k_mult(const float2* __restrict__ wper, const float2* __restrict__ E,
                                               float2* __restrict__ multT, int Ns, int N, int r) {
   const int R2 = 2 * r - 1;
-  __shared__ double2 wt[23 * 23];
-  __shared__ float4 T[23][MULT_XB];  // (hi.re, hi.im, lo.re, lo.im)
-  extern __shared__ float4 Es[];     // [R2][N] E as (hi.re, hi.im, lo.re, lo.im)
+  __shared__ float2 wt[23 * 23];
+  __shared__ float2 T[23][MULT_XB];
   const int x0 = blockIdx.x * MULT_XB;
   const int pk = blockIdx.y, l = blockIdx.z;
   int i = 0;
@@ -272,68 +254,43 @@ __global__ void __launch_bounds__(256) k_mult(const double2* __restrict__ wper, 
   const int j = i + (pk - mult_plane(i, i, Ns));
   const size_t fb = (size_t)l * Ns * Ns + (size_t)i * Ns + j;
   for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x) wt[e] = wper[fb * R2 * R2 + e];
-  for (int e = threadIdx.x; e < R2 * N; e += blockDim.x) {
-    const double2 v = E[e];
-    const float hx = (float)v.x, hy = (float)v.y;
-    Es[e] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
-  }
   __syncthreads();
   for (int e = threadIdx.x; e < R2 * MULT_XB; e += blockDim.x) {
     int dy = e / MULT_XB, xl = e - dy * MULT_XB;
-    double sr = 0.0, si = 0.0;
+    float2 s = cmk(0.f, 0.f);
     if (x0 + xl < N)
-      for (int dx = 0; dx < R2; ++dx) {
-        const double2 w = wt[dy * R2 + dx], ev = E[(size_t)dx * N + x0 + xl];
-        sr = fma(w.x, ev.x, fma(-w.y, ev.y, sr));
-        si = fma(w.x, ev.y, fma(w.y, ev.x, si));
-      }
-    const float hr = (float)sr, hi = (float)si;
-    T[dy][xl] = make_float4(hr, hi, (float)(sr - (double)hr), (float)(si - (double)hi));
+      for (int dx = 0; dx < R2; ++dx) cfma(s, wt[dy * R2 + dx], E[(size_t)dx * N + x0 + xl]);
+    T[dy][xl] = s;
   }
   __syncthreads();
   float2* out = multT + ((size_t)l * mult_planes(Ns) + pk) * N * N;
   for (int e = threadIdx.x; e < MULT_XB * N; e += blockDim.x) {
     int xl = e / N, y = e - xl * N;
     if (x0 + xl >= N) continue;
-    Df re{0.f, 0.f}, im{0.f, 0.f};
-    for (int dy = 0; dy < R2; ++dy) {
-      const float4 ev = Es[dy * N + y], t = T[dy][xl];
-      df_add_prod(re, ev.x, t.x);
-      df_add_prod(re, -ev.y, t.y);
-      df_add_prod(im, ev.x, t.y);
-      df_add_prod(im, ev.y, t.x);
-      re.lo = fmaf(ev.x, t.z, fmaf(ev.z, t.x, fmaf(-ev.y, t.w, fmaf(-ev.w, t.y, re.lo))));
-      im.lo = fmaf(ev.x, t.w, fmaf(ev.z, t.y, fmaf(ev.y, t.z, fmaf(ev.w, t.x, im.lo))));
-    }
-    float2 sv = cmk(re.hi + re.lo, im.hi + im.lo);
-    if (i == j) sv.y = 0.f;
-    out[(size_t)(x0 + xl) * N + y] = sv;
+    float2 s = cmk(0.f, 0.f);
+    for (int dy = 0; dy < R2; ++dy) cfma(s, E[(size_t)dy * N + y], T[dy][xl]);
+    if (i == j) s.y = 0.f;
+    out[(size_t)(x0 + xl) * N + y] = s;
   }
 }
 
-// W (FP64) -> hi + lo FP32 pairs
-__global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, float2* __restrict__ lo,
-                              size_t n) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const double2 v = in[e];
-    const float2 h = cmk((float)v.x, (float)v.y);
-    out[e] = h;
-    lo[e] = cmk((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
-  }
+__global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = cmk((float)in[e].x, (float)in[e].y);
 }
 
-smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, float2* Wlo, cudaStream_t s) {
-  k_c128_to_c64<<<128, 256, 0, s>>>(W64, W, Wlo, (size_t)P->LD * P->C * P->C);
+smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s) {
+  k_c128_to_c64<<<128, 256, 0, s>>>(W64, W, (size_t)P->LD * P->C * P->C);
   SMSM_LAUNCH_CHECK("k_c128_to_c64");
   return SMSM_OK;
 }
 
-smsm_status launch_filters(const smsm_plan_s* P, const float2* W, const float2* Wlo, cudaStream_t s) {
-  k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, Wlo, P->wcls, P->wper, P->Ns, P->r, P->C,
+smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s) {
+  k_filters<<<dim3(P->Ns, P->LD), 256, filters_smem(P), s>>>(W, P->wcls, P->wper, P->Ns, P->r, P->C,
                                                               !P->periodic);  // wcls holds the class taps dcls
   SMSM_LAUNCH_CHECK("k_filters");
   dim3 g2((P->N + MULT_XB - 1) / MULT_XB, mult_planes(P->Ns), P->LD);
-  k_mult<<<g2, 256, (size_t)P->R2 * P->N * sizeof(float4), s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
+  k_mult<<<g2, 256, 0, s>>>(P->wper, P->Etab, P->multT, P->Ns, P->N, P->r);
   SMSM_LAUNCH_CHECK("k_mult");
   return SMSM_OK;
 }
@@ -594,9 +551,8 @@ smsm_status band_init_attrs(const smsm_plan_s* P) {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_band_corner, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_filters, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mult, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess || band_smem(P) > 200 * 1024 || band_corner_smem(P) > 200 * 1024 ||
-      filters_smem(P) > 200 * 1024 || (size_t)P->R2 * P->N * sizeof(float4) > 200 * 1024) {
+      filters_smem(P) > 200 * 1024) {
     smsm_set_error("border-band kernel needs %zu bytes of shared memory", band_smem(P));
     return SMSM_ERR_ARG;
   }

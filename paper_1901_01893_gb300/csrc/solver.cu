@@ -297,12 +297,10 @@ static smsm_plan_s lane_view(const smsm_plan_s* P, int d0, int nd, int lane) {
   v.G64 += cc;
   v.V += cc;
   v.Wf += cc;
-  v.Wlo += cc;
   v.Gw += cc;
   v.Gw2 += cc;
   v.Gpart += cc * P->gram_nkx;
   v.eig += dd * L * Cp;
-  v.rotlog += dd * L * SMSM_MAX_SWEEPS * (Cp - 1) * (Cp / 2);
   v.sweeps += dd * L;
   v.wper += dd * L * Ns * Ns * R2 * R2;
   v.wcls += dd * L * R2 * R2 * Ns * Ns * R2 * R2;
@@ -358,7 +356,7 @@ static smsm_status enqueue_outer(smsm_plan_s* P, const smsm_params* prm, int k, 
   if ((st = launch_eig_weights(P, P->G64, k, prm, s, T))) return st;
   if (eig_done) SMSM_CUDA_TRY(cudaEventRecord(eig_done, s));
   T->begin(SMSM_STAGE_FILTERS);
-  if ((st = launch_filters(P, P->Wf, P->Wlo, s))) return st;
+  if ((st = launch_filters(P, P->Wf, s))) return st;
   T->end(SMSM_STAGE_FILTERS);
   if ((st = normal_pen_timed(P, P->xs, P->qv, lam, 0, s, T))) return st;
   T->begin(SMSM_STAGE_CG);
