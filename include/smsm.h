@@ -306,6 +306,29 @@ smsm_status smsm_fft2c(smsm_plan_t plan, const void* in, void* out, int count, i
 smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, int n, int filter,
                                      void* stream);
 
+/*
+ * Autotuner (not in the paper).  Times, on the plan's own data y (layout of
+ * smsm_reconstruct), the tensor-core Gram with each candidate number of split-K
+ * blocks (one to six waves of CTAs over the GPU) and short solves (two outer
+ * iterations of `params`) with 1..min(batch, SMSM_MAX_LANES) concurrent lanes,
+ * keeps the fastest of each for this plan (the lanes apply when params->lanes is 0)
+ * and remembers them for every later plan of the same shape (mb, shots, coils, N,
+ * filter, batch, precision, boundary, flags, CAIPI shift) in this process.
+ * Synchronises `stream`; `report` (host, nullable) receives what was timed.
+ * Results do not depend on the choices up to the order of the Gram's partial sums.
+ */
+typedef struct {
+  int gram_nG;              /* chosen split-K blocks (0: no tensor-core Gram) */
+  int n_gram;               /* candidates timed */
+  int gram_candidates[8];
+  float gram_ms[8];         /* device time of one Gram launch per candidate */
+  int lanes;                /* chosen lanes */
+  float lane_ms[SMSM_MAX_LANES]; /* device time of the short solve per lane count */
+} smsm_tune_report;
+
+smsm_status smsm_autotune(smsm_plan_t plan, const void* y, const smsm_params* params, smsm_tune_report* report,
+                          void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned warm start (not in the paper, which starts its iteration from the
  * data alone).  A complex CNN maps the aliased, zero-filled image of every

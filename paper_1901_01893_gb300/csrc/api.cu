@@ -241,8 +241,20 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   A(st, D);
   if (P->gram_tc) {
     P->gram_tc_nG = gram_tc_nG(P);
+    int cand[8];
+    const int nc = gram_tc_nG_candidates(P, cand, 8);
+    P->gram_nG_max = P->gram_tc_nG;
+    for (int k = 0; k < nc; ++k) P->gram_nG_max = cand[k] > P->gram_nG_max ? cand[k] : P->gram_nG_max;
+    int tnG = 0, tl = 0;
+    if (tune_cache_lookup(P, &tnG, &tl)) {  // an earlier plan of this shape was tuned
+      if (tnG > 0 && tnG <= P->gram_nG_max) P->gram_tc_nG = tnG;
+      P->tuned_lanes = tl;
+    }
     const size_t R2C = 2 * (size_t)gram_tc_cp(P);
-    A(Rpart, LD * P->gram_tc_nG * R2C * R2C);
+    A(Rpart, LD * P->gram_nG_max * R2C * R2C);
+  } else {
+    int tnG = 0, tl = 0;
+    if (tune_cache_lookup(P, &tnG, &tl)) P->tuned_lanes = tl;
   }
   if (P->alias) {
     A(acorr, alias_corr_count(P));
@@ -601,4 +613,15 @@ extern "C" smsm_status smsm_learned_start(smsm_plan_t plan, smsm_cnn_t cnn, cons
   if ((st = smsm_fft2c(plan, x_in, plan->bv, count, 1, stream))) return st;
   if ((st = smsm_cnn_forward(cnn, plan->bv, plan->pv, plan->D, stream))) return st;
   return smsm_fft2c(plan, plan->pv, x_out, count, 0, stream);
+}
+
+extern "C" smsm_status smsm_autotune(smsm_plan_t plan, const void* y, const smsm_params* params,
+                                     smsm_tune_report* report, void* stream) {
+  CHECK_PLAN("smsm_autotune");
+  CHECK_PTR("smsm_autotune", y);
+  smsm_status st;
+  if ((st = need_sens(plan, "smsm_autotune"))) return st;
+  smsm_params p;
+  if ((st = solve_params(plan, params, &p, "smsm_autotune"))) return st;
+  return solver_autotune(plan, y, &p, report, S(stream));
 }

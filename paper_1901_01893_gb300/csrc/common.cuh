@@ -103,7 +103,9 @@ struct smsm_plan_s {
   int precision;  // smsm_opts.precision
   int periodic;   // smsm_opts.boundary == PERIODIC: patch origins over all of [0, N)^2, mod N
   int gram_tc;    // 1: tensor-core Gram
-  int gram_tc_nG; // split-K partials of the tensor-core Gram
+  int gram_tc_nG; // split-K partials of the tensor-core Gram (the autotuner may change it)
+  int gram_nG_max; // split-K partials the Rpart buffer holds
+  int tuned_lanes; // lanes chosen by the autotuner (0: none; used when params->lanes == 0)
   float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials
   int alias;      // 1: column stage of A^H A through the per-class coil correlations
   float2* acorr;  // [N(x)][L Ns][L Ns][M(class)] coil correlations of the aliasing classes
@@ -266,6 +268,7 @@ smsm_status launch_gram(const smsm_plan_s* P, const float2* x, double2* G, cudaS
 int gram_tc_supported(const smsm_plan_s* P);
 int gram_tc_cp(const smsm_plan_s* P);
 int gram_tc_nG(const smsm_plan_s* P);
+int gram_tc_nG_candidates(const smsm_plan_s* P, int* out, int maxn);
 smsm_status gram_tc_init_attrs();
 smsm_status launch_gram_tc(const smsm_plan_s* P, const float2* x, double2* G, cudaStream_t s);
 smsm_status launch_filters(const smsm_plan_s* P, const float2* W, cudaStream_t s);
@@ -287,6 +290,9 @@ smsm_status cnn_shape(const smsm_cnn_s* c, int* B, int* H, int* W, int* maxn);
 int vec_blocks(const smsm_plan_s* P);
 smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const smsm_params* prm,
                                smsm_report* report, cudaStream_t s);
+smsm_status solver_autotune(smsm_plan_s* P, const void* y, const smsm_params* prm, smsm_tune_report* out,
+                            cudaStream_t s);
+int tune_cache_lookup(const smsm_plan_s* P, int* nG, int* lanes);
 void solver_free_timing(smsm_plan_s* P);
 smsm_status solver_reconstruct_groups(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
                                       const smsm_params* prm, smsm_report* reports, cudaStream_t s);

@@ -481,6 +481,41 @@ int gram_tc_nG(const smsm_plan_s* P) {
   return nG;
 }
 
+// Split-K block counts the autotuner tries: one to six waves of CTAs over the 152 SMs,
+// within the same bounds as the heuristic above (at least 2 patch rows per block, FP32
+// partials under 256 MB).  Returns the number written to out (at most maxn), ascending.
+int gram_tc_nG_candidates(const smsm_plan_s* P, int* out, int maxn) {
+  const int Cp = gram_tc_cp(P), R2C = 2 * Cp;
+  const int LD = P->LD, nsm = 152;
+  const int most = (P->P1 + 1) / 2;
+  const size_t per = (size_t)LD * R2C * R2C * sizeof(float);
+  int cap = (int)((size_t)256 * 1024 * 1024 / per);
+  if (cap < 1) cap = 1;
+  int n = 0;
+  const int heur = gram_tc_nG(P);
+  const double waves[] = {1.0, 2.0, 3.0, 4.0, 6.0};
+  int cand[8];
+  int nc = 0;
+  cand[nc++] = heur;
+  for (double w : waves) cand[nc++] = (int)std::ceil(w * nsm / LD);
+  for (int k = 0; k < nc; ++k) {
+    int v = cand[k];
+    if (v > most) v = most;
+    if (v > cap) v = cap;
+    if (v < 1) v = 1;
+    bool dup = false;
+    for (int j = 0; j < n; ++j) dup |= out[j] == v;
+    if (!dup && n < maxn) out[n++] = v;
+  }
+  for (int a = 1; a < n; ++a)  // ascending
+    for (int b = a; b > 0 && out[b] < out[b - 1]; --b) {
+      const int t = out[b];
+      out[b] = out[b - 1];
+      out[b - 1] = t;
+    }
+  return n;
+}
+
 static size_t gram_tc_smem(const smsm_plan_s* P) {
   return gram_tc_smem_for(P->C, P->Ns, P->r, P->N, P->periodic, gram_tc_prec(P));
 }

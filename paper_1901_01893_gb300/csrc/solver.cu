@@ -388,7 +388,7 @@ static smsm_status enqueue_outer(smsm_plan_s* P, const smsm_params* prm, int k, 
 
 // lanes actually used for these parameters
 static int solve_lanes(const smsm_plan_s* P, const smsm_params* prm) {
-  int n = prm->lanes > 0 ? prm->lanes : (P->D >= 9 ? 3 : (P->D >= 4 ? 2 : 1));
+  int n = prm->lanes > 0 ? prm->lanes : (P->tuned_lanes > 0 ? P->tuned_lanes : (P->D >= 9 ? 3 : (P->D >= 4 ? 2 : 1)));
   if (n > SMSM_MAX_LANES) n = SMSM_MAX_LANES;
   if (n > P->D) n = P->D;
   return n < 1 ? 1 : n;
@@ -626,5 +626,119 @@ smsm_status solver_sense(smsm_plan_s* P, const void* y, const void* phase, void*
     report->lanes = 1;
     report->lane0_batch = P->D;
   }
+  return SMSM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the split-K block count of the tensor-core Gram and the number of
+// concurrent lanes, timed on the plan's own data (y), chosen for the shortest
+// device time and remembered per shape for every later plan of that shape in
+// the process.
+// ---------------------------------------------------------------------------
+#include <map>
+#include <mutex>
+#include <tuple>
+
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int> TuneKey;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;
+
+static TuneKey tune_key(const smsm_plan_s* P) {
+  return TuneKey(P->L, P->Ns, P->Nc, P->N, P->r, P->D, P->precision, P->periodic, P->flags, P->Ldiv);
+}
+
+int tune_cache_lookup(const smsm_plan_s* P, int* nG, int* lanes) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(tune_key(P));
+  if (it == g_tune.end()) return 0;
+  *nG = it->second.first;
+  *lanes = it->second.second;
+  return 1;
+}
+
+smsm_status solver_autotune(smsm_plan_s* P, const void* y, const smsm_params* prm, smsm_tune_report* out,
+                            cudaStream_t s) {
+  smsm_tune_report rep;
+  memset(&rep, 0, sizeof(rep));
+  cudaEvent_t e0, e1;
+  SMSM_CUDA_TRY(cudaEventCreate(&e0));
+  SMSM_CUDA_TRY(cudaEventCreate(&e1));
+  smsm_status st = SMSM_OK;
+  float ms = 0.f;
+  // 1. the Gram's split-K blocks, on the starting point A^H y
+  if (P->gram_tc) {
+    const size_t ny = (size_t)P->D * P->Ns * P->Nc * P->M * P->N;
+    cudaError_t ce = cudaMemcpyAsync(P->ybuf, y, sizeof(float2) * ny, cudaMemcpyDeviceToDevice, s);
+    if (ce != cudaSuccess) st = SMSM_ERR_CUDA;
+    if (!st) st = launch_rowfft_out_T(P, P->ybuf, P->yh, P->D * P->Ns * P->Nc, P->M, 1, s);
+    if (!st) st = launch_col(P, COL_ADJ, 0, P->yh, P->hB, nullptr, nullptr, 0.f, nullptr, s);
+    if (!st) st = launch_rowfft_in_T(P, P->hB, P->xs, P->D * P->L * P->Ns, P->N, 0, s);
+    int cand[8];
+    const int nc = gram_tc_nG_candidates(P, cand, 8);
+    const int keep = P->gram_tc_nG;
+    float best = 1e30f;
+    int bestn = keep;
+    for (int k = 0; k < nc && !st && k < 8; ++k) {
+      if (cand[k] > P->gram_nG_max) continue;
+      P->gram_tc_nG = cand[k];
+      if ((st = launch_gram(P, P->xs, P->G64, s))) break;  // warm-up
+      SMSM_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int rep3 = 0; rep3 < 3 && !st; ++rep3) st = launch_gram(P, P->xs, P->G64, s);
+      SMSM_CUDA_TRY(cudaEventRecord(e1, s));
+      SMSM_CUDA_TRY(cudaEventSynchronize(e1));
+      SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 3.f;
+      rep.gram_candidates[rep.n_gram] = cand[k];
+      rep.gram_ms[rep.n_gram] = ms;
+      ++rep.n_gram;
+      if (ms < best) {
+        best = ms;
+        bestn = cand[k];
+      }
+    }
+    P->gram_tc_nG = st ? keep : bestn;
+    rep.gram_nG = P->gram_tc_nG;
+  }
+  // 2. the lanes, on a short solve (two outer iterations) of the same data
+  if (!st) {
+    smsm_params q = *prm;
+    q.outer_iters = prm->outer_iters < 2 ? prm->outer_iters : 2;
+    q.timing = 0;
+    q.warm = 0;
+    float best = 1e30f;
+    int bestl = 1;
+    const int maxl = P->D < SMSM_MAX_LANES ? P->D : SMSM_MAX_LANES;
+    for (int l = 1; l <= maxl && !st; ++l) {
+      q.lanes = l;
+      if ((st = solver_reconstruct(P, y, P->hA, &q, nullptr, s))) break;  // capture + warm-up
+      SMSM_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int rep2 = 0; rep2 < 2 && !st; ++rep2) st = solver_reconstruct(P, y, P->hA, &q, nullptr, s);
+      SMSM_CUDA_TRY(cudaEventRecord(e1, s));
+      SMSM_CUDA_TRY(cudaEventSynchronize(e1));
+      SMSM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 2.f;
+      rep.lane_ms[l - 1] = ms;
+      if (ms < best) {
+        best = ms;
+        bestl = l;
+      }
+    }
+    if (!st) {
+      P->tuned_lanes = bestl;
+      rep.lanes = bestl;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (P->has_graph) {  // the next solve captures with the chosen configuration
+    cudaGraphExecDestroy(P->gexec);
+    P->has_graph = 0;
+  }
+  if (st) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[tune_key(P)] = std::make_pair(P->gram_tc ? P->gram_tc_nG : 0, P->tuned_lanes);
+  }
+  if (out) *out = rep;
   return SMSM_OK;
 }

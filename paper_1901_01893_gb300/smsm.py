@@ -52,6 +52,11 @@ class Report(ctypes.Structure):
                 ("lanes", ctypes.c_int), ("lane0_batch", ctypes.c_int)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("gram_nG", ctypes.c_int), ("n_gram", ctypes.c_int), ("gram_candidates", ctypes.c_int * 8),
+                ("gram_ms", ctypes.c_float * 8), ("lanes", ctypes.c_int), ("lane_ms", ctypes.c_float * 4)]
+
+
 class SmsmError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"smsm status {status}: {msg}")
@@ -103,6 +108,8 @@ def lib() -> ctypes.CDLL:
     L.smsm_last_error.restype = ctypes.c_char_p
     L.smsm_default_params.argtypes = [ctypes.POINTER(Params)]
     L.smsm_default_params.restype = None
+    L.smsm_autotune.argtypes = [vp, vp, ctypes.POINTER(Params), ctypes.POINTER(TuneReport), vp]
+    L.smsm_autotune.restype = st
     L.smsm_cnn_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i]
     L.smsm_cnn_create.restype = st
     L.smsm_cnn_destroy.argtypes = [vp]
@@ -289,6 +296,18 @@ class Plan:
         return x, rep
 
     reconstruct = smsm_reconstruct
+
+    def smsm_autotune(self, y: torch.Tensor, params: Params | None = None) -> TuneReport:
+        """Time the Gram's split-K blocks and the lane count on y; keep (and cache per shape)
+        the fastest.  Returns what was timed."""
+        if params is None:
+            params = default_params()
+        rep = TuneReport()
+        _check(lib().smsm_autotune(self._h, _dev(y, self.y_shape, "y"), ctypes.byref(params), ctypes.byref(rep),
+                                   _stream()))
+        return rep
+
+    autotune = smsm_autotune
 
     def smsm_sense(self, y: torch.Tensor, phase: torch.Tensor | None = None, cg_iters: int = 30,
                    x: torch.Tensor | None = None, report: bool = True):

@@ -29,7 +29,7 @@ import functools
 
 import numpy as np
 
-__all__ = ["CONFIGS", "make_group", "coords", "bandlimited_phase"]
+__all__ = ["CONFIGS", "make_group", "coords", "bandlimited_phase", "draw_phase_coeffs", "phase_from_coeffs"]
 
 # Workloads: the acquisitions the paper reconstructs (Methods: 128x128, 32
 # channels, MB 2-3, 2- and 4-shot, filter 4x4 / 6x6), at the sizes the tests
@@ -154,3 +154,50 @@ def bandlimited_phase(rng: np.random.Generator, L: int, Ns: int, N: int, s: int)
     DC and transforms with its own centred DFT.
     """
     return (rng.standard_normal((L, Ns, s, s)) + 1j * rng.standard_normal((L, Ns, s, s)))
+
+
+def draw_phase_coeffs(rng: np.random.Generator, L: int, Ns: int, field: bool, kmax: int = 3) -> dict:
+    """The random coefficients of one direction's shot phases (the draws of _poly_phase and
+    _field for every slice and shot), without rasterising them: poly [L][Ns][10] (the a + b <= 3
+    monomials in the order of _poly_phase) and, with ``field``, band [L][Ns][2k+1][2k+1]
+    complex (zero outside |k| <= kmax).  For workloads with many directions, whose phases are
+    then rasterised on the device by phase_from_coeffs."""
+    poly = np.zeros((L, Ns, 10))
+    band = np.zeros((L, Ns, 2 * kmax + 1, 2 * kmax + 1), dtype=np.complex128) if field else None
+    for l in range(L):
+        for i in range(Ns):
+            poly[l, i] = rng.uniform(-np.pi, np.pi, size=10)
+            if field:
+                for ky in range(-kmax, kmax + 1):
+                    for kx in range(-kmax, kmax + 1):
+                        if kx * kx + ky * ky <= kmax * kmax:
+                            band[l, i, ky + kmax, kx + kmax] = rng.standard_normal() + 1j * rng.standard_normal()
+    return {"poly": poly, "band": band}
+
+
+def phase_from_coeffs(coefs: dict, N: int, xp=np, device=None):
+    """exp(j (polynomial [+ field])) for coefficients from draw_phase_coeffs, with the array
+    namespace ``xp`` (numpy, or torch for a device tensor): the same formulas as
+    _poly_phase and _field."""
+    def arr(a):
+        return xp.asarray(a) if xp is np else xp.as_tensor(a, device=device)
+    u = coords(N)
+    U = arr(u / 2)
+    poly = arr(coefs["poly"])  # [L][Ns][10]
+    X = U[None, :]
+    Y = U[:, None]
+    ph = 0
+    t = 0
+    for a in range(4):
+        for b in range(4 - a):
+            ph = ph + poly[..., t, None, None] * (X ** a) * (Y ** b)
+            t += 1
+    if coefs["band"] is not None:
+        kmax = (coefs["band"].shape[-1] - 1) // 2
+        k = np.arange(-kmax, kmax + 1)
+        E = arr(np.exp(1j * np.pi * np.outer(k, u)))   # [k][n]
+        C = arr(coefs["band"])                         # [L][Ns][ky][kx]
+        f = (E.T @ C @ E).real                         # [L][Ns][y][x]
+        m = f.abs().amax(dim=(-2, -1), keepdim=True) if xp is not np else np.abs(f).max(axis=(-2, -1), keepdims=True)
+        ph = ph + f * (np.pi / m)
+    return xp.exp(1j * ph)

@@ -489,3 +489,35 @@ def test_bf16_split_precision_form(smsm):
     err = slice_err(xr.cpu().numpy(), ref)
     print("BF16 split solve NRMSE vs FP64 oracle (worst slice)", err)
     assert err < BF16_TOL
+
+
+def test_autotune_picks_a_candidate_and_keeps_the_results(smsm):
+    # The tuner times the Gram's split-K candidates and 1..4 lanes on the plan's data and keeps
+    # the fastest; the solve is unchanged up to the order of the Gram's partial sums, and a later
+    # plan of the same shape starts from the cached choice.
+    key = "tiny"
+    L, Ns, Nc, N, r, Ldiv = CASES[key]
+    D = 6
+    g, xt, y0 = _problem(key, 12)
+    rng = np.random.default_rng(61)
+    ys = c64(np.stack([y0 * np.exp(1j * 0.3 * d) + 0.05 * crandn(rng, *y0.shape) for d in range(D)]))
+    prm = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4)
+    p0 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    p0.set_sens(c64(g["sens"]))
+    x0, _ = p0.reconstruct(ys, params=prm)
+    p1 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)
+    p1.set_sens(c64(g["sens"]))
+    rep = p1.autotune(ys, params=prm)
+    cands = list(rep.gram_candidates)[:rep.n_gram]
+    print("autotune: Gram split-K", cands, [round(v, 3) for v in list(rep.gram_ms)[:rep.n_gram]], "->", rep.gram_nG,
+          "; lanes ms", [round(v, 3) for v in rep.lane_ms], "->", rep.lanes)
+    assert rep.n_gram >= 2 and rep.gram_nG in cands
+    assert 1 <= rep.lanes <= 4 and rep.lane_ms[rep.lanes - 1] == min(v for v in rep.lane_ms if v > 0)
+    x1, r1 = p1.reconstruct(ys, params=prm)
+    assert r1.status == 0 and r1.lanes == rep.lanes
+    assert slice_err(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-6
+    p2 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)  # same shape: the cached choice
+    p2.set_sens(c64(g["sens"]))
+    x2, r2 = p2.reconstruct(ys, params=prm)
+    assert r2.lanes == rep.lanes
+    assert torch.equal(x1, x2)

@@ -93,3 +93,21 @@ def test_plan_rejects_unknown_options(lib):
         h = ctypes.c_void_p()
         assert lib.smsm_plan(ctypes.byref(h), 2, 4, 8, 64, 64, 5, ctypes.byref(opts)) == smsm.SMSM_ERR_ARG
         assert not h.value
+
+
+def test_network_tuner_and_learned_start_check_arguments(lib):
+    from paper_1901_01893_gb300 import smsm
+
+    h = ctypes.c_void_p()
+    # channel, width, layer, size and batch ranges are checked before any CUDA call
+    for args in ((0, 64, 6, 32, 32, 1), (4, 0, 6, 32, 32, 1), (4, 64, 0, 32, 32, 1), (4, 64, 6, 0, 32, 1),
+                 (4, 64, 6, 32, 32, 0), (300, 64, 6, 32, 32, 1)):
+        assert lib.smsm_cnn_create(ctypes.byref(h), *args) == smsm.SMSM_ERR_ARG
+        assert not h.value
+    assert lib.smsm_cnn_create(None, 4, 8, 2, 16, 16, 1) == smsm.SMSM_ERR_ARG
+    assert lib.smsm_cnn_param_count(None) == 0
+    assert lib.smsm_cnn_destroy(None) == smsm.SMSM_OK
+    assert lib.smsm_cnn_forward(None, None, None, 1, None) == smsm.SMSM_ERR_ARG
+    assert lib.smsm_cnn_train_step(None, None, None, 1, ctypes.c_float(1e-3), None, None) == smsm.SMSM_ERR_ARG
+    assert lib.smsm_learned_start(None, None, None, None, None) == smsm.SMSM_ERR_ARG
+    assert lib.smsm_autotune(None, None, None, None, None) == smsm.SMSM_ERR_ARG
