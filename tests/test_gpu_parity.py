@@ -515,7 +515,7 @@ def test_autotune_picks_a_candidate_and_keeps_the_results(smsm):
     assert 1 <= rep.lanes <= 4 and rep.lane_ms[rep.lanes - 1] == min(v for v in rep.lane_ms if v > 0)
     x1, r1 = p1.reconstruct(ys, params=prm)
     assert r1.status == 0 and r1.lanes == rep.lanes
-    assert slice_err(x1.cpu().numpy(), x0.cpu().numpy()) < 1e-6
+    assert slice_err(x1.cpu().numpy(), x0.cpu().numpy()) < SOLVE_TOL  # FP32 rounding of another split-K order
     p2 = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, batch=D)  # same shape: the cached choice
     p2.set_sens(c64(g["sens"]))
     x2, r2 = p2.reconstruct(ys, params=prm)
