@@ -496,7 +496,7 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 
 BATCHED_GROUPS, BATCHED_DIRECTIONS = 20, 60
-FILTER_FOR_SHOTS = {2: 4, 4: 6, 8: 4}  # the paper's 4x4 (2 shots) and 6x6 (4 shots); 4x4 for 8 shots
+FILTER_FOR_SHOTS = {2: 4, 4: 6, 8: 6}  # the paper's 4x4 (2 shots) and 6x6 (4 shots); 8 shots keep 6x6
 
 
 def batched_geometries(seed=4, n=BATCHED_GROUPS):

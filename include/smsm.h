@@ -97,9 +97,14 @@ typedef enum { SMSM_BOUNDARY_VALID = 0, SMSM_BOUNDARY_PERIODIC = 1 } smsm_bounda
  *                    path exists;
  *   PER_COIL_NORMAL: the column stage of A^H A loops over the coils with two
  *                    M-point transforms per coil instead of applying the
- *                    per-class coil correlations (which need N % caipi_div == 0). */
+ *                    per-class coil correlations (which need N % caipi_div == 0);
+ *   CLUSTER_EIG: the eigen step by one-sided block Jacobi on a cluster of eight
+ *                CTAs per Gram (C = shots*filter^2 >= 65) even where the two-CTA
+ *                two-sided solver fits.  C > 168 always takes the cluster solver
+ *                (G of up to 320 x 320 does not fit one CTA's shared memory). */
 #define SMSM_FLAG_GENERIC_KERNELS 1
 #define SMSM_FLAG_PER_COIL_NORMAL 2
+#define SMSM_FLAG_CLUSTER_EIG 4
 
 /*
  * Solver parameters.  The paper minimises Eq. 10 with an augmented-Lagrangian
@@ -122,9 +127,8 @@ typedef struct {
   int mode;           /* smsm_mode */
   int rank;           /* NULLSPACE rank, 0 < rank < C */
   int warm;           /* 1: x holds the starting point on entry; 0: start from A^H y */
-  int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 30 (the most the rotation
-                         log holds); reaching it with rotations pending sets
-                         SMSM_ERR_EIG_UNCONVERGED */
+  int max_sweeps;     /* cap on Jacobi sweeps of the eigen step, 0 -> 30 (at most 30);
+                         reaching it with rotations pending sets SMSM_ERR_EIG_UNCONVERGED */
   int timing;         /* bitmask of (1 << smsm_stage): bracket those launches with CUDA
                          events inside the solve and report their device time */
   int eig_cold;       /* 1: restart the eigensolver from scratch every outer iteration
@@ -135,7 +139,11 @@ typedef struct {
                          lanes' CG runs; 0 -> automatic (3 for a batch of at least 9, 2
                          from 4), at most SMSM_MAX_LANES and the batch.  Results do not
                          depend on it. */
-  int reserved[3];
+  float eig_tol;      /* rotation threshold of the Jacobi eigen step, relative (a pair is rotated
+                         while its coupling exceeds eig_tol times the geometric mean of its
+                         diagonal terms); 0 -> 1e-6 for the two-CTA solver, 2e-6 for the
+                         cluster solver (whose pair sums carry ~1e-7 relative rounding) */
+  int reserved[2];
 } smsm_params;
 
 #define SMSM_MAX_LANES 4
@@ -147,7 +155,7 @@ typedef enum {
   SMSM_STAGE_ADJOINT = 0,    /* b = A^H y (row FFT, column stage, row FFT) */
   SMSM_STAGE_GRAM = 1,       /* Hankel Gram partials + reduction */
   SMSM_STAGE_EIG = 2,        /* Jacobi sweeps on G */
-  SMSM_STAGE_VAPPLY = 3,     /* eigenvectors from the rotation log */
+  SMSM_STAGE_VAPPLY = 3,     /* Newton-Schulz re-orthonormalisation of V */
   SMSM_STAGE_WEIGHTS = 4,    /* eps schedule + W */
   SMSM_STAGE_FILTERS = 5,    /* filters from W + image-domain multipliers */
   SMSM_STAGE_ROWFFT_INV = 6, /* x-direction inverse FFT of the CG vector */

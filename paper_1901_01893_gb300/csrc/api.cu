@@ -141,8 +141,11 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   }
   const int C = shots * r * r;
   const int Cp = C + (C & 1);
-  if (C > SMSM_MAX_C || eig_jacobi_smem(Cp) > 227 * 1024) {
-    smsm_set_error("smsm_plan: shots*filter^2 = %d is above the eigensolver's shared-memory limit (166)", C);
+  const int flags = opts ? opts->flags : 0;
+  const int eig_cluster = !eig_pair_supported(Cp) || (flags & SMSM_FLAG_CLUSTER_EIG);
+  if (C > SMSM_MAX_C || (eig_cluster && !eig_cluster_supported(C))) {
+    smsm_set_error("smsm_plan: shots*filter^2 = %d is outside the eigensolver's range (at most %d; at least 65 "
+                   "with SMSM_FLAG_CLUSTER_EIG)", C, SMSM_MAX_C);
     return SMSM_ERR_ARG;
   }
   const int caipi_div = (opts && opts->caipi_div > 0) ? opts->caipi_div : mb;
@@ -168,7 +171,8 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
   P->Ldiv = caipi_div;
   P->D = D;
   P->LD = D * mb;
-  P->flags = opts ? opts->flags : 0;
+  P->flags = flags;
+  P->eig_cluster = eig_cluster;
   P->precision = opts ? opts->precision : SMSM_PRECISION_FP32;
   if (P->precision != SMSM_PRECISION_FP32 && P->precision != SMSM_PRECISION_BF16_SPLIT) {
     free(P);
@@ -333,7 +337,7 @@ extern "C" smsm_status smsm_plan(smsm_plan_t* out, int mb, int shots, int coils,
       st = SMSM_ERR_CUDA;
     }
   }
-  if (!st) st = eig_init_attrs(Cp);
+  if (!st) st = eig_init_attrs(P);
   if (!st && smsm_col_smem_bytes(P) > 200 * 1024) {
     smsm_set_error("smsm_plan: column stage would need %zu bytes of shared memory", smsm_col_smem_bytes(P));
     st = SMSM_ERR_ARG;
@@ -527,10 +531,10 @@ static smsm_status solve_params(smsm_plan_t plan, const smsm_params* params, sms
       !(p->lambda >= 0.0) || !(p->eps0_rel > 0.0) || !(p->eps_min_rel > 0.0) ||
       (p->mode != SMSM_MODE_IRLS && p->mode != SMSM_MODE_NULLSPACE) ||
       (p->mode == SMSM_MODE_NULLSPACE && (p->rank <= 0 || p->rank >= plan->C)) || p->lanes < 0 ||
-      p->lanes > SMSM_MAX_LANES) {
+      p->lanes > SMSM_MAX_LANES || !(p->eig_tol >= 0.f && p->eig_tol < 1.f)) {
     smsm_set_error("%s: invalid parameters (K in [0,%d], J >= 0, eta >= 1, lambda >= 0, "
-                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C), lanes in [0, %d])", fn, SMSM_MAX_OUTER,
-                   SMSM_MAX_LANES);
+                   "eps0_rel, eps_min_rel > 0, NULLSPACE rank in (0, C), lanes in [0, %d], eig_tol in [0, 1))", fn,
+                   SMSM_MAX_OUTER, SMSM_MAX_LANES);
     return SMSM_ERR_ARG;
   }
   return SMSM_OK;

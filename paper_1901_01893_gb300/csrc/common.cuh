@@ -106,6 +106,7 @@ struct smsm_plan_s {
   int gram_tc_nG; // split-K partials of the tensor-core Gram (the autotuner may change it)
   int gram_nG_max; // split-K partials the Rpart buffer holds
   int tuned_lanes; // lanes chosen by the autotuner (0: none; used when params->lanes == 0)
+  int eig_cluster; // 1: eigen step by one-sided block Jacobi on an 8-CTA cluster (C > 168, or asked for)
   float* Rpart;   // [LD][nG][2Cp][2Cp] tensor-core Gram partials
   int alias;      // 1: column stage of A^H A through the per-class coil correlations
   float2* acorr;  // [N(x)][L Ns][L Ns][M(class)] coil correlations of the aliasing classes
@@ -278,8 +279,13 @@ smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2*
 // eig.cu
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T);
-smsm_status eig_init_attrs(int Cp);
+smsm_status eig_init_attrs(const smsm_plan_s* P);
 size_t eig_jacobi_smem(int Cp);
+bool eig_pair_supported(int Cp);
+bool eig_cluster_supported(int C);
+smsm_status eig_cluster_init_attrs(int C);
+smsm_status launch_eig_cluster(const smsm_plan_s* P, const double2* G, const float2* T, int max_sweeps, float tol,
+                               float floor_rel, cudaStream_t s);
 smsm_status operators_init_attrs();
 size_t smsm_col_smem_bytes(const smsm_plan_s* P);
 int band_blocks(const smsm_plan_s* P);

@@ -30,23 +30,10 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "jacobi.cuh"
 #include "umma.cuh"
 
 #define CG_T 16  // tile edge of the small complex GEMMs (weights, warm-start congruence)
-
-__device__ __forceinline__ void jpair(int round, int k, int Cp, int& p, int& q) {
-  const int m = Cp - 1;
-  int a, b;
-  if (k == 0) {
-    a = 0;
-    b = 1 + (round % m);
-  } else {
-    a = 1 + ((k + round) % m);
-    b = 1 + ((m - k + round) % m);
-  }
-  p = min(a, b);
-  q = max(a, b);
-}
 
 __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z == 1.f && J.w == 0.f; }
 
@@ -95,48 +82,7 @@ __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, 
 // on a timeout the waiting side raises the device error flag (SMSM_ERR_TIMEOUT) and
 // goes on, and both CTAs meet at a final cluster barrier, so neither leaves while the
 // other may still touch its shared memory.
-#define JAC_MAXWAIT (1L << 22)
 #define JAC_VS 3  // pair slots per lane of the V-CTA: Cp/2 <= 32 JAC_VS (Cp <= 192)
-
-__device__ __forceinline__ uint32_t cl_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cl_map(const void* p, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
-  return r;
-}
-__device__ __forceinline__ void cl_st_v4(uint32_t a, float4 v) {
-  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
-}
-__device__ __forceinline__ void cl_st_s32(uint32_t a, int v) {
-  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ void cl_arrive(uint32_t remote_mbar, uint32_t count) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(remote_mbar), "r"(count)
-               : "memory");
-}
-// bounded wait on a local mbarrier phase, acquiring what the other CTA released
-__device__ __forceinline__ bool cl_wait(uint64_t* mbar, uint32_t parity) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
-  for (long it = 0; it < JAC_MAXWAIT; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        "selp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void cl_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // shared-memory layout (bytes), the same in both CTAs: region A holds G (rank 0) or V
 // (rank 1), both with row stride Cp + 1; region B holds rank 0's rotation, p and q
@@ -561,10 +507,17 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
 }
 
 
-smsm_status eig_init_attrs(int Cp) {
+// the two-CTA solver holds all of G in one CTA's shared memory (C up to 168)
+bool eig_pair_supported(int Cp) {
   const int nh = (Cp / 2 + 1) & ~1;
-  if ((nh / 2) * (nh + 1) > JAC_BLK * 1024) {
-    smsm_set_error("Jacobi kernel: C = %d is above its block schedule's limit", Cp);
+  return (nh / 2) * (nh + 1) <= JAC_BLK * 1024 && Cp / 2 <= 32 * JAC_VS && jac_smem_bytes(Cp) <= 227 * 1024;
+}
+
+smsm_status eig_init_attrs(const smsm_plan_s* P) {
+  if (P->eig_cluster) return eig_cluster_init_attrs(P->C);
+  const int Cp = P->Cp;
+  if (!eig_pair_supported(Cp)) {
+    smsm_set_error("Jacobi kernel: C = %d is above the two-CTA solver's limit", Cp);
     return SMSM_ERR_ARG;
   }
   const size_t sm = jac_smem_bytes(Cp);
@@ -586,6 +539,17 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   // warm start from the previous outer iteration's eigenvectors (same solve)
   const int warm = (outer > 0 && !prm->eig_cold) ? 1 : 0;
   if (T) T->begin(SMSM_STAGE_EIG);
+  if (P->eig_cluster) {
+    // one-sided Jacobi on A = G V_prev (the congruence's first product) or on G itself
+    if (warm) {
+      dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
+      k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
+      SMSM_LAUNCH_CHECK("k_congruence");
+    }
+    const float tol = prm->eig_tol > 0.f ? prm->eig_tol : 2e-6f;
+    smsm_status st = launch_eig_cluster(P, G, warm ? P->Gw : nullptr, msw, tol, 1e-12f, s);
+    if (st) return st;
+  } else {
   if (warm) {
     dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
     k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
@@ -600,8 +564,10 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   const double frel = 1e-12;
   // two CTAs per matrix: the Jacobi rounds on G and, beside them, V times every rotation
   k_jacobi<<<2 * P->LD, 1024, jac_smem_bytes(Cp), s>>>(G, warm ? P->Gw2 : nullptr, P->eig, P->V, warm, P->sweeps, C,
-                                                        Cp, msw, 1e-6f, (float)frel, P->st, P->L, P->devflag);
+                                                        Cp, msw, prm->eig_tol > 0.f ? prm->eig_tol : 1e-6f,
+                                                        (float)frel, P->st, P->L, P->devflag);
   SMSM_LAUNCH_CHECK("k_jacobi");
+  }
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
   {

@@ -21,6 +21,7 @@ SMSM_ERR_EIG_UNCONVERGED = 8
 SMSM_MODE_IRLS, SMSM_MODE_NULLSPACE = 0, 1
 SMSM_FLAG_GENERIC_KERNELS = 1
 SMSM_FLAG_PER_COIL_NORMAL = 2
+SMSM_FLAG_CLUSTER_EIG = 4
 SMSM_BOUNDARY_VALID = 0
 SMSM_BOUNDARY_PERIODIC = 1
 SMSM_PRECISION_FP32, SMSM_PRECISION_BF16_SPLIT = 0, 1
@@ -40,7 +41,7 @@ class Params(ctypes.Structure):
                 ("eps_min_rel", ctypes.c_double), ("outer_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
                 ("mode", ctypes.c_int), ("rank", ctypes.c_int), ("warm", ctypes.c_int),
                 ("max_sweeps", ctypes.c_int), ("timing", ctypes.c_int), ("eig_cold", ctypes.c_int),
-                ("lanes", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("lanes", ctypes.c_int), ("eig_tol", ctypes.c_float), ("reserved", ctypes.c_int * 2)]
 
 
 class Report(ctypes.Structure):

@@ -51,7 +51,7 @@ def test_default_params(lib):
     (2, 4, 8, 70, 70, 5),      # 70 = 2*5*7 is not 2^a 3^b
     (2, 4, 8, 64, 64, 0),      # filter < 1
     (2, 4, 8, 64, 64, 13),     # filter too large
-    (2, 8, 8, 64, 64, 6),      # C = 288 > 160 (eigensolver limit)
+    (2, 8, 8, 64, 64, 7),      # C = 392 > 320
     (2, 16, 8, 64, 64, 2),     # more than 8 shots
 ])
 def test_plan_rejects_bad_geometry(lib, args):
