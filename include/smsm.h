@@ -260,10 +260,15 @@ smsm_status smsm_reconstruct(smsm_plan_t plan, const void* y, void* x, const sms
 
 /*
  * Independent slice groups that may differ in geometry (MB, shots, coils, N,
- * filter; one plan each, coil maps set) reconstructed together: every plan's
- * captured solve (as smsm_reconstruct, same params for all) runs on that plan's
- * own stream, forked from `stream` and joined back into it, so the kernels of
- * small and large groups share the GPU.  ys[k], xs[k] are laid out as for
+ * filter; one plan each, coil maps set) reconstructed together in ONE graph launch
+ * on `stream`: a graph holding, for every group, the copy of its y (and warm start)
+ * in, its captured solve (as smsm_reconstruct, same params for all) as a child
+ * graph and the copy of x out, the groups as independent branches, so the kernels
+ * of small and large groups share the GPU.  The graph is built on the first call
+ * with a given list of plans, buffers and params and reused while they stay the
+ * same (a few such lists are kept; destroying a plan drops those holding it).  With
+ * params->timing set, each group's solve is launched on its own stream instead,
+ * forked from `stream` and joined back into it.  ys[k], xs[k] are laid out as for
  * smsm_reconstruct on plans[k]; a plan may appear only once, and every plan must
  * belong to the current device.  `reports`
  * (nullable) is an array of n, filled after a synchronisation of `stream`.

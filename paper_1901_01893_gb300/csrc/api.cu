@@ -99,7 +99,8 @@ static void free_plan(smsm_plan_s* P) {
                   P->Rpart, P->devflag, P->acorr, P->ash};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (P->has_graph) cudaGraphExecDestroy(P->gexec);
+  solver_forget_plan(P);
+  solver_drop_graph(P);
   solver_free_timing(P);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   for (int k = 0; k < SMSM_MAX_LANES; ++k)

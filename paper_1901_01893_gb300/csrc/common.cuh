@@ -143,8 +143,10 @@ struct smsm_plan_s {
   SolverState* st;   // [D]
   DevReport* rep;
   size_t bytes;
-  // graph cache for smsm_reconstruct
+  // graph cache for smsm_reconstruct: the captured solve and its instantiation
+  cudaGraph_t graph;
   cudaGraphExec_t gexec;
+  unsigned graph_gen;  // bumped whenever the captured solve is dropped (group launches re-check it)
   cudaStream_t cap_stream;
   cudaStream_t lane_s[SMSM_MAX_LANES];  // capture streams of lanes 1.. (lane 0 captures on cap_stream)
   cudaEvent_t lane_ev[2 * SMSM_MAX_LANES + 1];  // fork, per-lane join and eigen-step events
@@ -277,6 +279,8 @@ smsm_status launch_band(const smsm_plan_s* P, const float2* x, float2* out, floa
                         cudaStream_t s);
 smsm_status launch_w_from_c128(const smsm_plan_s* P, const double2* W64, float2* W, cudaStream_t s);
 // eig.cu
+void solver_drop_graph(smsm_plan_s* P);
+void solver_forget_plan(smsm_plan_s* P);
 smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer, const smsm_params* prm,
                                cudaStream_t s, Timer* T);
 smsm_status eig_init_attrs(const smsm_plan_s* P);

@@ -520,8 +520,10 @@ smsm_status eig_init_attrs(const smsm_plan_s* P) {
     smsm_set_error("Jacobi kernel: C = %d is above the two-CTA solver's limit", Cp);
     return SMSM_ERR_ARG;
   }
+  // the attribute belongs to the kernel, not to the plan: set the most any plan uses, so a
+  // plan made later with a smaller C does not shrink it under an earlier plan's launches
   const size_t sm = jac_smem_bytes(Cp);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jac_smem_bytes(168));
   if (e != cudaSuccess) {
     smsm_set_error("Jacobi kernel cannot get %zu bytes of shared memory: %s", sm, cudaGetErrorString(e));
     return SMSM_ERR_ARG;

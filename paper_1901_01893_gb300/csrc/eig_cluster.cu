@@ -290,7 +290,9 @@ smsm_status eig_cluster_init_attrs(int C) {
     smsm_set_error("cluster eigensolver: C = %d outside [65, %d]", C, SMSM_MAX_C);
     return SMSM_ERR_ARG;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osj_smem(C));
+  // per kernel, not per plan: the most any C of this instance (same C/32 rounded up) uses
+  const int cmax = 32 * osj_kr(C) < SMSM_MAX_C ? 32 * osj_kr(C) : SMSM_MAX_C;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osj_smem(cmax));
   if (e != cudaSuccess) {
     smsm_set_error("cluster eigensolver cannot get %zu bytes of shared memory: %s", osj_smem(C),
                    cudaGetErrorString(e));

@@ -10,6 +10,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -446,12 +447,17 @@ static smsm_status enqueue_solve(smsm_plan_s* P, const smsm_params* prm, cudaStr
 static bool same_params(const smsm_params* a, const smsm_params* b) { return memcmp(a, b, sizeof(*a)) == 0; }
 
 // Capture (once per parameter set) and instantiate the plan's solve graph.
+void solver_drop_graph(smsm_plan_s* P) {
+  if (!P->has_graph) return;
+  cudaGraphExecDestroy(P->gexec);
+  cudaGraphDestroy(P->graph);
+  P->has_graph = 0;
+  ++P->graph_gen;
+}
+
 static smsm_status ensure_graph(smsm_plan_s* P, const smsm_params* prm) {
   if (!P->has_graph || !same_params(&P->gparams, prm)) {
-    if (P->has_graph) {
-      cudaGraphExecDestroy(P->gexec);
-      P->has_graph = 0;
-    }
+    solver_drop_graph(P);
     cudaGraph_t g;
     SMSM_CUDA_TRY(cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal));
     smsm_status st = enqueue_solve(P, prm, P->cap_stream);
@@ -472,11 +478,12 @@ static smsm_status ensure_graph(smsm_plan_s* P, const smsm_params* prm) {
     }
     P->graph_kernels = nk;
     ce = cudaGraphInstantiate(&P->gexec, g, 0);
-    cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
+      cudaGraphDestroy(g);
       smsm_set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
       return SMSM_ERR_CUDA;
     }
+    P->graph = g;  // kept: the group launch embeds it as a child graph
     P->gparams = *prm;
     P->has_graph = 1;
   }
@@ -545,11 +552,154 @@ smsm_status solver_reconstruct(smsm_plan_s* P, const void* y, void* x, const sms
 // Independent slice groups, possibly of different geometry (one plan each), solved
 // concurrently: every plan's graph runs on the plan's own stream, forked from s and
 // joined back into it, so the kernels of small and large groups share the GPU.
+// One graph for a whole call of smsm_reconstruct_groups: per group the copy of y in
+// (and of the warm start), the group's captured solve as a child graph bracketed by its
+// timing events, and the copy of x out; the groups are independent branches, so a single
+// graph launch runs every group concurrently.  Instantiated graphs are kept for the
+// most recent lists of plans (same captured solves); a call with other y or x buffers
+// only re-points the copy nodes.  A plan's destruction drops the graphs holding it.
+struct GroupExec {
+  std::vector<smsm_plan_s*> plans;
+  std::vector<unsigned> gens;
+  std::vector<const void*> ys;
+  std::vector<void*> xs;
+  std::vector<cudaGraphNode_t> in_y, in_x, out;  // copy nodes of each group (in_x: warm start only)
+  int warm;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+static std::mutex g_group_mu;
+static std::vector<GroupExec> g_groups;
+#define GROUP_CACHE 8
+
+static void free_group(GroupExec& ge) {
+  if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  if (ge.graph) cudaGraphDestroy(ge.graph);
+}
+
+void solver_forget_plan(smsm_plan_s* P) {
+  std::lock_guard<std::mutex> lock(g_group_mu);
+  for (size_t i = 0; i < g_groups.size();) {
+    bool has = false;
+    for (smsm_plan_s* q : g_groups[i].plans) has = has || q == P;
+    if (has) {
+      free_group(g_groups[i]);
+      g_groups.erase(g_groups.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+static size_t group_nx(const smsm_plan_s* P) { return sizeof(float2) * P->D * P->L * P->Ns * P->N * P->N; }
+static size_t group_ny(const smsm_plan_s* P) { return sizeof(float2) * P->D * P->Ns * P->Nc * P->M * P->N; }
+
+static cudaError_t build_group_exec(GroupExec& ge) {
+  cudaError_t e = cudaGraphCreate(&ge.graph, 0);
+  if (e != cudaSuccess) return e;
+  const size_t n = ge.plans.size();
+  ge.in_y.assign(n, nullptr);
+  ge.in_x.assign(n, nullptr);
+  ge.out.assign(n, nullptr);
+  for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+    smsm_plan_s* P = ge.plans[k];
+    cudaGraphNode_t in[2], e0, child, e1;
+    int nin = 1;
+    e = cudaGraphAddMemcpyNode1D(&in[0], ge.graph, nullptr, 0, P->ybuf, ge.ys[k], group_ny(P),
+                                 cudaMemcpyDeviceToDevice);
+    ge.in_y[k] = in[0];
+    if (e == cudaSuccess && ge.warm) {
+      e = cudaGraphAddMemcpyNode1D(&in[1], ge.graph, nullptr, 0, P->xs, ge.xs[k], group_nx(P),
+                                   cudaMemcpyDeviceToDevice);
+      ge.in_x[k] = in[1];
+      nin = 2;
+    }
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&e0, ge.graph, in, nin, P->ev0);
+    if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&child, ge.graph, &e0, 1, P->graph);
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&e1, ge.graph, &child, 1, P->ev1);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&ge.out[k], ge.graph, &e1, 1, ge.xs[k], P->xs, group_nx(P),
+                                   cudaMemcpyDeviceToDevice);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+  return e;
+}
+
+// point the copy nodes of an instantiated group graph at this call's buffers
+static cudaError_t repoint_group(GroupExec& ge, const void* const* ys, void* const* xs) {
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < ge.plans.size() && e == cudaSuccess; ++k) {
+    smsm_plan_s* P = ge.plans[k];
+    if (ge.ys[k] != ys[k]) {
+      e = cudaGraphExecMemcpyNodeSetParams1D(ge.exec, ge.in_y[k], P->ybuf, ys[k], group_ny(P),
+                                             cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess) ge.ys[k] = ys[k];
+    }
+    if (e == cudaSuccess && ge.xs[k] != xs[k]) {
+      if (ge.warm)
+        e = cudaGraphExecMemcpyNodeSetParams1D(ge.exec, ge.in_x[k], P->xs, xs[k], group_nx(P),
+                                               cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess)
+        e = cudaGraphExecMemcpyNodeSetParams1D(ge.exec, ge.out[k], xs[k], P->xs, group_nx(P),
+                                               cudaMemcpyDeviceToDevice);
+      if (e == cudaSuccess) ge.xs[k] = xs[k];
+    }
+  }
+  return e;
+}
+
+// the instantiated group graph of this call (built on first use); nullptr when it cannot
+// be built, and the call then falls back to one graph launch per group on forked streams
+static cudaGraphExec_t group_exec(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
+                                  int warm) {
+  std::lock_guard<std::mutex> lock(g_group_mu);
+  for (size_t i = 0; i < g_groups.size(); ++i) {
+    GroupExec& ge = g_groups[i];
+    if ((int)ge.plans.size() != n || ge.warm != warm) continue;
+    bool same = true;
+    for (int k = 0; k < n && same; ++k) same = ge.plans[k] == plans[k] && ge.gens[k] == plans[k]->graph_gen;
+    if (!same) continue;
+    if (repoint_group(ge, ys, xs) == cudaSuccess) return ge.exec;
+    cudaGetLastError();
+    free_group(ge);
+    g_groups.erase(g_groups.begin() + i);
+    break;
+  }
+  GroupExec ge;
+  ge.plans.assign(plans, plans + n);
+  for (int k = 0; k < n; ++k) ge.gens.push_back(plans[k]->graph_gen);
+  ge.ys.assign(ys, ys + n);
+  ge.xs.assign(xs, xs + n);
+  ge.warm = warm;
+  ge.graph = nullptr;
+  ge.exec = nullptr;
+  if (build_group_exec(ge) != cudaSuccess) {
+    cudaGetLastError();
+    free_group(ge);
+    return nullptr;
+  }
+  if (g_groups.size() >= GROUP_CACHE) {
+    free_group(g_groups.front());
+    g_groups.erase(g_groups.begin());
+  }
+  g_groups.push_back(ge);
+  return ge.exec;
+}
+
 smsm_status solver_reconstruct_groups(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
                                       const smsm_params* prm, smsm_report* reports, cudaStream_t s) {
   smsm_status st;
   for (int k = 0; k < n; ++k)
     if ((st = ensure_graph(plans[k], prm))) return st;
+  // timed solves carry their own event records: those stay on the per-group path
+  cudaGraphExec_t ex = prm->timing ? nullptr : group_exec(n, plans, ys, xs, prm->warm ? 1 : 0);
+  if (ex) {
+    SMSM_CUDA_TRY(cudaGraphLaunch(ex, s));
+    if (reports)
+      for (int k = 0; k < n; ++k)
+        if ((st = fill_report(plans[k], prm, &reports[k], s))) return st;
+    return SMSM_OK;
+  }
   cudaEvent_t fork = plans[0]->lane_ev[0];
   SMSM_CUDA_TRY(cudaEventRecord(fork, s));
   for (int k = 0; k < n; ++k) {
@@ -730,10 +880,7 @@ smsm_status solver_autotune(smsm_plan_s* P, const void* y, const smsm_params* pr
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (P->has_graph) {  // the next solve captures with the chosen configuration
-    cudaGraphExecDestroy(P->gexec);
-    P->has_graph = 0;
-  }
+  solver_drop_graph(P);  // the next solve captures with the chosen configuration
   if (st) return st;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -138,13 +138,15 @@ def _check(status: int) -> None:
         raise SmsmError(status, lib().smsm_last_error().decode())
 
 
-def reconstruct_groups(plans, ys, params: Params | None = None, report: bool = True):
-    """Solve independent groups of possibly different geometry together (one plan each):
-    returns ([x_k], [Report_k] or None)."""
+def reconstruct_groups(plans, ys, params: Params | None = None, report: bool = True, xs=None):
+    """Solve independent groups of possibly different geometry together (one plan each, one
+    graph launch): returns ([x_k], [Report_k] or None).  xs: output tensors to reuse (they
+    also hold the warm starts when params.warm is set)."""
     n = len(plans)
     if params is None:
         params = default_params()
-    xs = [torch.empty(p.x_shape, dtype=torch.complex64, device=y.device) for p, y in zip(plans, ys)]
+    if xs is None:
+        xs = [torch.empty(p.x_shape, dtype=torch.complex64, device=y.device) for p, y in zip(plans, ys)]
     hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
     hy = (ctypes.c_void_p * n)(*[_dev(y, p.y_shape, "y") for p, y in zip(plans, ys)])
     hx = (ctypes.c_void_p * n)(*[_dev(x, p.x_shape, "x") for p, x in zip(plans, xs)])

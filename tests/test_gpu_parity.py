@@ -360,7 +360,9 @@ def test_sms_sense_parity(smsm, with_phase):
 
 def test_groups_of_different_geometry_match_single_solves(smsm):
     # Two slice groups of different geometry (64^2 MB 2 4-shot; 48^2 MB 3 2-shot)
-    # solved together on their own streams give exactly their single-plan results.
+    # solved together in one graph launch give exactly their single-plan results; so
+    # does the same call again with other data buffers (the cached group graph re-pointed),
+    # and the per-group stream path taken when the solve is timed.
     prm = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4)
     plans, ys, singles = [], [], []
     for key, seed in (("tiny", 3), ("radix3", 4)):
@@ -377,6 +379,17 @@ def test_groups_of_different_geometry_match_single_solves(smsm):
     for k in range(len(plans)):
         assert reps[k].status == 0
         assert np.array_equal(xs[k].cpu().numpy(), singles[k])
+    # other y buffers, reused x buffers holding stale values
+    ys2 = [y.clone() for y in ys]
+    xs2, reps = smsm.reconstruct_groups(plans, ys2, params=prm, xs=xs)
+    for k in range(len(plans)):
+        assert xs2[k] is xs[k] and reps[k].status == 0 and reps[k].elapsed_ms > 0
+        assert np.array_equal(xs2[k].cpu().numpy(), singles[k])
+    prm_t = smsm.default_params(lam=1e-2, outer_iters=3, cg_iters=4, timing=1 << 2)
+    xs3, reps = smsm.reconstruct_groups(plans, ys2, params=prm_t)
+    for k in range(len(plans)):
+        assert reps[k].status == 0 and reps[k].stage_ms[2] > 0
+        assert np.array_equal(xs3[k].cpu().numpy(), singles[k])
 
 
 def test_lanes_give_identical_results(smsm):
