@@ -50,7 +50,7 @@ __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z ==
 // triangle is an (n/2) x (n+1) rectangle of block indices.
 // warm != 0: start from Gw = V_prev^H G V_prev (symmetrised on load).
 
-#define JAC_BLK 4  // blocks per thread: (Cp/2 rounded to even)/2 * (that + 1) <= 4 * 1024 for Cp <= 180
+#define JAC_BLK 4  // blocks per thread: (Cp/2 rounded to even)/2 * (that + 1) <= 4 * 992 for Cp <= 168
 
 // block bi of the folded triangle -> (k1, k2), k1 <= k2 < n (n even)
 __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, int& k2) {
@@ -78,7 +78,9 @@ __device__ __forceinline__ void tri_block(int bi, int n, float inv_n1, int& k1, 
 // of rotations is written.  Rank 0 sends round m's rotations into rank 1's shared
 // memory (buffer m & 1) and arrives on rank 1's `full` mbarrier; rank 1 applies them
 // and arrives on rank 0's `empty` mbarrier, which rank 0 waits for before it reuses
-// the buffer.  A message with header -1 ends the exchange.  Every wait is bounded:
+// the buffer.  The sending is the last warp's only job: the other 31 warps update G's
+// blocks meanwhile, so the latency of the remote stores and of the release stays off the
+// round's critical path.  A message with header -1 ends the exchange.  Every wait is bounded:
 // on a timeout the waiting side raises the device error flag (SMSM_ERR_TIMEOUT) and
 // goes on, and both CTAs meet at a final cluster barrier, so neither leaves while the
 // other may still touch its shared memory.
@@ -106,8 +108,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   unsigned char* regb = jsm + jac_region_a(Cp);
   float4* rbuf = reinterpret_cast<float4*>(regb);                      // rank 1: [2][half]
   if (tid == 0) {
-    mbar_init(&full_b[0], (uint32_t)half);
-    mbar_init(&full_b[1], (uint32_t)half);
+    mbar_init(&full_b[0], 32);  // one arrival per lane of rank 0's sender warp
+    mbar_init(&full_b[1], 32);
     mbar_init(&empty_b[0], 1);
     mbar_init(&empty_b[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -199,10 +201,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   int* rq = rp + half;
   const uint32_t r_buf = cl_map(rbuf, 1), r_hdr = cl_map(hdr, 1);
   const uint32_t r_full0 = cl_map(&full_b[0], 1), r_full1 = cl_map(&full_b[1], 1);
-  long msg = 0;  // messages sent to rank 1
+  long msg = 0;  // messages sent to rank 1 (counted by the sender warp)
   bool link = true;
-  // send round `round` (or -1: the end) from the rotation table; the writers of a message
-  // are the threads tid < half (each arrives once), the end message is thread 0's alone
+  const int nbt = nt - 32;  // threads with blocks of G; the last warp sends
+  const int lane = tid & 31;
+  // send round `round` (or -1: the end) from the rotation table: the sender warp's lanes
+  // write it (lane k the rotations k, k + 32, ...) and each arrives once; the end message
+  // is lane 0's alone (one arrival counting for all 32)
   auto send = [&](int round) {
     const int b = (int)(msg & 1);
     if (msg >= 2 && link && !cl_wait(&empty_b[b], (uint32_t)(((msg >> 1) - 1) & 1))) {
@@ -210,12 +215,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
       atomicExch(errflag, SMSM_ERR_TIMEOUT);
     }
     if (round >= 0) {
-      cl_st_v4(r_buf + (uint32_t)((b * half + tid) * sizeof(float4)), rot[tid]);
-      if (tid == 0) cl_st_s32(r_hdr + (uint32_t)(b * sizeof(int)), round);
+      for (int k = lane; k < half; k += 32) cl_st_v4(r_buf + (uint32_t)((b * half + k) * sizeof(float4)), rot[k]);
+      if (lane == 0) cl_st_s32(r_hdr + (uint32_t)(b * sizeof(int)), round);
       cl_arrive(b ? r_full1 : r_full0, 1);
-    } else {
+    } else if (lane == 0) {
       cl_st_s32(r_hdr + (uint32_t)(b * sizeof(int)), -1);
-      cl_arrive(b ? r_full1 : r_full0, (uint32_t)half);
+      cl_arrive(b ? r_full1 : r_full0, 32);
     }
     ++msg;
   };
@@ -245,9 +250,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   int kb1[JAC_BLK], kb2[JAC_BLK];
 #pragma unroll
   for (int m = 0; m < JAC_BLK; ++m) {
-    const int bi = tid + m * nt;
+    const int bi = tid + m * nbt;
     kb1[m] = kb2[m] = -1;
-    if (bi < nblk) {
+    if (tid < nbt && bi < nblk) {
       tri_block(bi, nh, inv_n1, kb1[m], kb2[m]);
       if (kb2[m] >= half) kb1[m] = -1;  // virtual pair of an odd half
     }
@@ -256,10 +261,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   int pending = 1;  // the last sweep (or the direct test after it) found a pair to rotate
   for (; sw < max_sweeps; ++sw) {
     int rotated = 0;  // this thread set a non-identity rotation during the sweep
+    // this thread's pair of the round-robin (tid < half): both indices advance by one
+    // (mod Cp - 1, over 1..Cp-1) from round to round, index 0 stays with pair 0
+    int pa = 0, pb = 0;
+    if (tid < half) jpair(0, tid, Cp, pa, pb);
     for (int round = 0; round < Cp - 1; ++round) {
       if (tid < half) {
-        int p, q;
-        jpair(round, tid, Cp, p, q);
+        const int p = min(pa, pb), q = max(pa, pb);
         rp[tid] = p;
         rq[tid] = q;
         const float a = g[p * ld + p].x, d = g[q * ld + q].x;
@@ -267,18 +275,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
         const float babs = hypotf(b.x, b.y);
         float4 J = make_float4(1.f, 0.f, 1.f, 0.f);
         if (babs > floor_abs && babs > tol * sqrtf(fabsf(a * d))) {
-          const float theta = (d - a) / (2.f * babs);
-          const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-          const float c = 1.f / sqrtf(t * t + 1.f);
-          J = make_float4(c, t * c, b.x / babs, -b.y / babs);
+          // one correctly rounded reciprocal and one reciprocal square root instead of
+          // four divisions
+          const float ib = __frcp_rn(babs);
+          const float theta = 0.5f * (d - a) * ib;
+          const float t = copysignf(__frcp_rn(fabsf(theta) + sqrtf(fmaf(theta, theta, 1.f))), theta);
+          const float c = __frsqrt_rn(fmaf(t, t, 1.f));
+          J = make_float4(c, t * c, b.x * ib, -b.y * ib);
           rotated = 1;
         }
         rot[tid] = J;
-        send(round);
-      } else {
-        ++msg;  // every thread counts the messages (only the writers use the count)
+        pb = pb == Cp - 1 ? 1 : pb + 1;
+        if (tid > 0) pa = pa == Cp - 1 ? 1 : pa + 1;
       }
       __syncthreads();
+      if (tid >= nbt) send(round);  // the sender warp, while the others update G
 #pragma unroll
       for (int m = 0; m < JAC_BLK; ++m) {
         const int k1 = kb1[m], k2 = kb2[m];
@@ -356,7 +367,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   for (int j = tid; j < Cp; j += nt) eig[(size_t)l * Cp + j] = g[j * ld + j].x;
   if (tid == 0) sweeps_out[l] = sw;
   __syncthreads();  // rank 1 reads the last rounds' buffers until it sees the end message
-  if (tid == 0) send(-1);
+  if (tid >= nbt) send(-1);
   __syncthreads();
   cl_sync();
 }
@@ -510,7 +521,7 @@ __global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, c
 // the two-CTA solver holds all of G in one CTA's shared memory (C up to 168)
 bool eig_pair_supported(int Cp) {
   const int nh = (Cp / 2 + 1) & ~1;
-  return (nh / 2) * (nh + 1) <= JAC_BLK * 1024 && Cp / 2 <= 32 * JAC_VS && jac_smem_bytes(Cp) <= 227 * 1024;
+  return (nh / 2) * (nh + 1) <= JAC_BLK * (1024 - 32) && Cp / 2 <= 32 * JAC_VS && jac_smem_bytes(Cp) <= 227 * 1024;
 }
 
 smsm_status eig_init_attrs(const smsm_plan_s* P) {
