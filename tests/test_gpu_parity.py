@@ -62,7 +62,8 @@ CASES = {
     "odd_shots": (1, 3, 4, 96, 3, 1),  # Ns = 3, M = 32, one slice
     "mb3_8shots": (3, 8, 6, 64, 3, 3),  # M = 8, C = 72
     "r1": (2, 2, 3, 32, 1, 2),         # filter 1: C = Ns
-    "maxc": (2, 2, 4, 64, 9, 2),       # largest C the eigensolver takes: C = Cp = 162 (FMA Gram)
+    "maxc": (2, 2, 4, 64, 9, 2),       # C = Cp = 162: FMA Gram, the two-CTA eigensolver's range
+    "c294": (2, 6, 4, 48, 7, 2),       # C = 294 (10 row groups of 32): FMA Gram, cluster eigensolver
     "maxn": (1, 2, 2, 512, 2, 1),      # largest image edge, N = 512
 }
 
@@ -117,7 +118,7 @@ def test_fft2c_parity(smsm, key):
     assert O.nrmse(back, img) < OP_TOL
 
 
-@pytest.mark.parametrize("key", ["tiny", "plain", "radix3", "mb3_8shots", "r1", "maxc", "maxn"])
+@pytest.mark.parametrize("key", ["tiny", "plain", "radix3", "mb3_8shots", "r1", "maxc", "c294", "maxn"])
 def test_gram_parity(smsm, key):
     plan, S, rng = make_plan(smsm, key)
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -152,7 +153,8 @@ def _random_weight(rng, L, C):
     return (A + np.conj(np.swapaxes(A, 1, 2))) / np.sqrt(C)
 
 
-@pytest.mark.parametrize("key", ["tiny", "plain", "precision", "radix3", "mb3_8shots", "r1", "maxc", "maxn"])
+@pytest.mark.parametrize("key", ["tiny", "plain", "precision", "radix3", "mb3_8shots", "r1", "maxc", "c294",
+                                 "maxn"])
 def test_apply_filters_parity(smsm, key):
     plan, S, rng = make_plan(smsm, key)
     L, Ns, Nc, N, r, Ldiv = CASES[key]
@@ -201,7 +203,7 @@ def _problem(key, seed):
 
 
 @pytest.mark.parametrize("key,K,J", [("tiny", 3, 4), ("radix3", 3, 5), ("plain", 2, 3), ("r1", 3, 4),
-                                     ("maxc", 2, 3), ("maxn", 2, 3)])
+                                     ("maxc", 2, 3), ("c294", 3, 4), ("maxn", 2, 3)])
 def test_reconstruct_parity(smsm, key, K, J):
     L, Ns, Nc, N, r, Ldiv = CASES[key]
     g, xt, y = _problem(key, 1)
@@ -220,13 +222,16 @@ def test_reconstruct_parity(smsm, key, K, J):
     assert torch.equal(x, x2)
 
 
-def test_reconstruct_nullspace_mode(smsm):
+@pytest.mark.parametrize("cluster", [False, True])
+def test_reconstruct_nullspace_mode(smsm, cluster):
+    # the projector onto the C - rank smallest eigenvectors, with either eigensolver
     key = "tiny"
     L, Ns, Nc, N, r, Ldiv = CASES[key]
     g, xt, y = _problem(key, 2)
     rank = 40
     ref = O.reconstruct(y, g["sens"], r, dict(K=3, J=5, lam=1e-1, mode="nullspace", rank=rank), Ldiv=Ldiv)
-    plan, _, _ = make_plan(smsm, key, sens=g["sens"])
+    plan = smsm.Plan(L, Ns, Nc, N, r, caipi_div=Ldiv, flags=smsm.SMSM_FLAG_CLUSTER_EIG if cluster else 0)
+    plan.set_sens(c64(g["sens"]))
     prm = smsm.default_params(lam=1e-1, outer_iters=3, cg_iters=5, mode=smsm.SMSM_MODE_NULLSPACE, rank=rank)
     x, rep = plan.reconstruct(c64(y), params=prm)
     assert rep.status == 0

@@ -55,13 +55,29 @@ WORK = {
 }
 
 
+def _needed(request):
+    """The workloads whose oracle solves the selected tests of this module read."""
+    need = set()
+    for item in request.session.items:
+        if item.module is not request.module:
+            continue
+        cs = getattr(item, "callspec", None)
+        if cs is not None and "key" in cs.params:
+            need.add(cs.params["key"])
+        elif item.originalname == "test_bf16_split_solve_per_slice":
+            need.add("precision")
+    return need
+
+
 @pytest.fixture(scope="module")
-def refs():
+def refs(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    ex = cf.ProcessPoolExecutor(max_workers=len(WORK), mp_context=mp.get_context("spawn"))
+    need = _needed(request)
+    ex = cf.ProcessPoolExecutor(max_workers=max(1, len(need)), mp_context=mp.get_context("spawn"))
     # the largest first, so it has the most time
-    futs = {k: ex.submit(J.solve, *WORK[k][:8], WORK[k][8], LAM) for k in ("precision", "plain", "eight_shots", "tiny")}
+    order = [k for k in ("precision", "plain", "eight_shots", "tiny") if k in need]
+    futs = {k: ex.submit(J.solve, *WORK[k][:8], WORK[k][8], LAM) for k in order}
     yield futs
     ex.shutdown(wait=False, cancel_futures=True)
 
