@@ -35,6 +35,31 @@ __device__ __forceinline__ void dft4(float2* v) {
   v[3] = csub(d02, rot);
 }
 
+// 8-point DFT in registers, natural order in and out: two 4-point DFTs of the even and odd
+// elements, the odd ones turned by w8^k (w8 = exp(-+ 2 pi i / 8)), then one radix-2 step
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float h = 0.707106781186547524f;  // sqrt(1/2)
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<INV>(e);
+  dft4<INV>(o);
+  // forward: w8 = h (1 - i), w8^2 = -i, w8^3 = h (-1 - i); inverse: their conjugates
+  const float2 o1 = INV ? cmk(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                        : cmk(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+  const float2 o2 = INV ? cmk(-o[2].y, o[2].x) : cmk(o[2].y, -o[2].x);
+  const float2 o3 = INV ? cmk(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                        : cmk(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
 template <bool INV>
 __device__ __forceinline__ void dft3(float2* v) {
   // X1 = a0 - t1/2 -+ i (sqrt3/2) t2, X2 = a0 - t1/2 +- i (sqrt3/2) t2, t1 = a1+a2, t2 = a1-a2
@@ -48,11 +73,12 @@ __device__ __forceinline__ void dft3(float2* v) {
   v[2] = csub(m, j);
 }
 
-// One radix-R pass (R in {2, 3, 4}) of the Stockham FFT described above, with
+// One radix-R pass (R in {2, 3, 4, 8}) of the Stockham FFT described above, with
 // the transform length N, R and the product S of the earlier radices fixed at
 // compile time (so every index division is by a constant); then the next pass.
-// Radices are taken in the order 4, ..., 4, 2, ..., 2, 3, ..., 3, the same
-// order as the runtime descriptor, so both give identical results.
+// Radices are taken in the order 8, ..., 8, 4, 2, 3, ..., 3: fewer passes through
+// shared memory than the runtime descriptor's 4, ..., 4, 2, 3, ..., 3 (used only for
+// the lengths without a fixed chain).
 template <bool INV, int N, int S>
 __device__ __forceinline__ float2* fft_fixed_from(float2* src, float2* dst, int nbatch, int bstride,
                                                   const float2* tw) {
@@ -60,7 +86,7 @@ __device__ __forceinline__ float2* fft_fixed_from(float2* src, float2* dst, int 
     return src;
   } else {
     constexpr int REM = N / S;
-    constexpr int R = (REM % 4 == 0) ? 4 : ((REM % 2 == 0) ? 2 : 3);
+    constexpr int R = (REM % 8 == 0) ? 8 : ((REM % 4 == 0) ? 4 : ((REM % 2 == 0) ? 2 : 3));
     constexpr int nR = N / R;
     constexpr int tstep = N / (S * R);
     const int ntask = nbatch * nR;
@@ -78,7 +104,9 @@ __device__ __forceinline__ float2* fft_fixed_from(float2* src, float2* dst, int 
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_get<INV>(tw, r * k * tstep));
       }
-      if constexpr (R == 4)
+      if constexpr (R == 8)
+        dft8<INV>(v);
+      else if constexpr (R == 4)
         dft4<INV>(v);
       else if constexpr (R == 2)
         dft2<INV>(v);
