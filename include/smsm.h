@@ -322,8 +322,9 @@ smsm_status smsm_hankel_gram_noalloc(const void* x, void* G, int mb, int shots, 
 /*
  * Autotuner (not in the paper).  Times, on the plan's own data y (layout of
  * smsm_reconstruct), the tensor-core Gram with each candidate number of split-K
- * blocks (one to six waves of CTAs over the GPU) and short solves (two outer
- * iterations of `params`) with 1..min(batch, SMSM_MAX_LANES) concurrent lanes,
+ * blocks (one to six waves of CTAs over the GPU) and shortened solves (min(K, 6)
+ * outer iterations of `params`, so that the cold first eigen step weighs about as
+ * little as in the full solve) with 1..min(batch, SMSM_MAX_LANES) concurrent lanes,
  * keeps the fastest of each for this plan (the lanes apply when params->lanes is 0)
  * and remembers them for every later plan of the same shape (mb, shots, coils, N,
  * filter, batch, precision, boundary, flags, CAIPI shift) in this process.
@@ -336,7 +337,7 @@ typedef struct {
   int gram_candidates[8];
   float gram_ms[8];         /* device time of one Gram launch per candidate */
   int lanes;                /* chosen lanes */
-  float lane_ms[SMSM_MAX_LANES]; /* device time of the short solve per lane count */
+  float lane_ms[SMSM_MAX_LANES]; /* device time of the shortened solve per lane count */
 } smsm_tune_report;
 
 smsm_status smsm_autotune(smsm_plan_t plan, const void* y, const smsm_params* params, smsm_tune_report* report,
