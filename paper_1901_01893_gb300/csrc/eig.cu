@@ -33,7 +33,6 @@
 #include "jacobi.cuh"
 #include "umma.cuh"
 
-#define CG_T 16  // tile edge of the small complex GEMMs (weights, warm-start congruence)
 
 __device__ __forceinline__ bool is_ident(float4 J) { return J.y == 0.f && J.z == 1.f && J.w == 0.f; }
 
@@ -372,75 +371,128 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   cl_sync();
 }
 
-// Warm start: Gw = V^H G V (two tiled complex GEMMs per matrix, FP32 accumulate).
-// step 0: T = G V (G in FP64, rounded on load); step 1: Gw = V^H T.
-__global__ void __launch_bounds__(256) k_congruence(const double2* __restrict__ G, const float2* __restrict__ V,
-                                                    const float2* __restrict__ Tin, float2* __restrict__ out, int C,
-                                                    int step) {
-  __shared__ float2 As[CG_T][CG_T + 1];
-  __shared__ float2 Bs[CG_T][CG_T + 1];
-  const int l = blockIdx.z;
-  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
-  const int a = blockIdx.y * CG_T + ty, b = blockIdx.x * CG_T + tx;
+// The small complex GEMMs of the eigen step, C x C per matrix, FP32 accumulation:
+//   SG_GV:  T  = G V            (G in FP64, rounded on load; the warm start's first product)
+//   SG_VHT: Gw = V^H T          (the warm start's second product)
+//   SG_VHV: M  = V^H V          (Newton-Schulz, step 0)
+//   SG_NS:  V' = V (3I - M) / 2 (Newton-Schulz, step 1)
+//   SG_W:   W  = V diag(f) V^H, f_j = (max(s_j, 0) + eps)^(-1/2) (IRLS) or
+//           [s_j among the C - rank smallest] (NULLSPACE)
+// A CTA computes a 32 x 32 output tile, each thread 2 x 2 entries (rows ty, ty + 16, columns
+// tx, tx + 16), over k-steps of 16 staged in shared memory; every operand tile is loaded
+// along its contiguous index.
+#define SG_T 32
+#define SG_K 16
+enum { SG_GV = 0, SG_VHT = 1, SG_VHV = 2, SG_NS = 3, SG_W = 4 };
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_cgemm(const double2* __restrict__ G, const float2* __restrict__ X,
+                                               const float2* __restrict__ Y, float2* __restrict__ out, int C,
+                                               const float* __restrict__ eig, const SolverState* __restrict__ st,
+                                               int Cp, int mode, int rank, int L) {
+  __shared__ float2 As[SG_T][SG_K + 1];
+  __shared__ float2 Bs[SG_K][SG_T + 1];
+  __shared__ float f[OP == SG_W ? SMSM_MAX_C : 1];
+  const int l = blockIdx.z;  // flat (direction, slice)
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int a0 = blockIdx.y * SG_T, b0 = blockIdx.x * SG_T;
   const size_t off = (size_t)l * C * C;
-  float2 acc = cmk(0.f, 0.f);
-  for (int k0 = 0; k0 < C; k0 += CG_T) {
-    // A tile: rows a-block, cols k;  B tile: rows k, cols b-block
-    const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
-    const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
-    float2 av = cmk(0.f, 0.f), bv = cmk(0.f, 0.f);
-    if (ar < C && ak < C) {
-      if (step == 0) {
-        const double2 gv = G[off + (size_t)ar * C + ak];
-        av = cmk((float)gv.x, (float)gv.y);
+  const float2* Xl = X + off;
+  if constexpr (OP == SG_W) {
+    const float* s = eig + (size_t)l * Cp;
+    const double eps = st[l / L].eps;
+    for (int j = tid; j < C; j += blockDim.x) {
+      if (mode == SMSM_MODE_NULLSPACE) {
+        int rk = 0;
+        const float sj = s[j];
+        for (int k = 0; k < C; ++k) rk += (s[k] < sj) || (s[k] == sj && k < j);
+        f[j] = rk < C - rank ? 1.f : 0.f;
       } else {
-        av = conjf2(V[off + (size_t)ak * C + ar]);  // (V^H)[ar][ak] = conj(V[ak][ar])
+        f[j] = (float)(1.0 / sqrt(fmax((double)s[j], 0.0) + eps));
       }
     }
-    if (bk < C && bc < C) bv = step == 0 ? V[off + (size_t)bk * C + bc] : Tin[off + (size_t)bk * C + bc];
-    As[ty][tx] = av;
-    Bs[ty][tx] = bv;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
     __syncthreads();
   }
-  if (a < C && b < C) out[off + (size_t)a * C + b] = acc;
+  // A is read along k (row-contiguous) except for V^H, read along a
+  constexpr bool a_rows = !(OP == SG_VHT || OP == SG_VHV);
+  // B is read along b except for conj(V)^T of the weights, read along k
+  constexpr bool b_rows = OP != SG_W;
+  float2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = cmk(0.f, 0.f);
+  for (int k0 = 0; k0 < C; k0 += SG_K) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int t = tid + 256 * it;
+      const int al = a_rows ? t / SG_K : t % SG_T, kl = a_rows ? t % SG_K : t / SG_T;
+      const int a = a0 + al, k = k0 + kl;
+      float2 v = cmk(0.f, 0.f);
+      if (a < C && k < C) {
+        if constexpr (OP == SG_GV) {
+          const double2 g = G[off + (size_t)a * C + k];
+          v = cmk((float)g.x, (float)g.y);
+        } else if constexpr (OP == SG_VHT || OP == SG_VHV) {
+          v = conjf2(Xl[(size_t)k * C + a]);
+        } else if constexpr (OP == SG_NS) {
+          v = Xl[(size_t)a * C + k];
+        } else {
+          v = cscale(Xl[(size_t)a * C + k], f[k]);
+        }
+      }
+      As[al][kl] = v;
+    }
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int t = tid + 256 * it;
+      const int bl = b_rows ? t % SG_T : t / SG_K, kl = b_rows ? t / SG_T : t % SG_K;
+      const int b = b0 + bl, k = k0 + kl;
+      float2 v = cmk(0.f, 0.f);
+      if (b < C && k < C) {
+        if constexpr (OP == SG_GV || OP == SG_VHV) {
+          v = Xl[(size_t)k * C + b];
+        } else if constexpr (OP == SG_VHT) {
+          v = Y[off + (size_t)k * C + b];
+        } else if constexpr (OP == SG_NS) {
+          const float2 m = Y[off + (size_t)k * C + b];
+          v = cmk(((k == b ? 3.f : 0.f) - m.x) * 0.5f, -0.5f * m.y);
+        } else {
+          v = conjf2(Xl[(size_t)b * C + k]);
+        }
+      }
+      Bs[kl][bl] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SG_K; ++k) {
+      const float2 x0 = As[ty][k], x1 = As[ty + 16][k];
+      const float2 y0 = Bs[k][tx], y1 = Bs[k][tx + 16];
+      cfma(acc[0][0], x0, y0);
+      cfma(acc[0][1], x0, y1);
+      cfma(acc[1][0], x1, y0);
+      cfma(acc[1][1], x1, y1);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < C && b < C) out[off + (size_t)a * C + b] = acc[i][j];
+    }
 }
 
-
-// Newton-Schulz re-orthonormalisation of V (one step squares the orthogonality error):
-// step 0: M = V^H V;  step 1: out = V (3I - M) / 2.  16 x 16 output tiles, FP32.
-__global__ void __launch_bounds__(256) k_ns(const float2* __restrict__ V, const float2* __restrict__ M,
-                                            float2* __restrict__ out, int C, int step) {
-  __shared__ float2 As[CG_T][CG_T + 1];
-  __shared__ float2 Bs[CG_T][CG_T + 1];
-  const int l = blockIdx.z;
-  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
-  const int a = blockIdx.y * CG_T + ty, b = blockIdx.x * CG_T + tx;
-  const size_t off = (size_t)l * C * C;
-  float2 acc = cmk(0.f, 0.f);
-  for (int k0 = 0; k0 < C; k0 += CG_T) {
-    const int ar = blockIdx.y * CG_T + ty, ak = k0 + tx;
-    const int bk = k0 + ty, bc = blockIdx.x * CG_T + tx;
-    float2 av = cmk(0.f, 0.f), bv = cmk(0.f, 0.f);
-    if (ar < C && ak < C) av = step == 0 ? conjf2(V[off + (size_t)ak * C + ar]) : V[off + (size_t)ar * C + ak];
-    if (bk < C && bc < C) {
-      if (step == 0) {
-        bv = V[off + (size_t)bk * C + bc];
-      } else {
-        const float2 m = M[off + (size_t)bk * C + bc];
-        bv = cmk(((bk == bc ? 3.f : 0.f) - m.x) * 0.5f, -0.5f * m.y);
-      }
-    }
-    As[ty][tx] = av;
-    Bs[ty][tx] = bv;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
-    __syncthreads();
-  }
-  if (a < C && b < C) out[off + (size_t)a * C + b] = acc;
+template <int OP>
+static smsm_status launch_cgemm(const smsm_plan_s* P, const double2* G, const float2* X, const float2* Y,
+                                float2* out, const smsm_params* prm, cudaStream_t s) {
+  const int C = P->C;
+  const dim3 grid((C + SG_T - 1) / SG_T, (C + SG_T - 1) / SG_T, P->LD);
+  k_cgemm<OP><<<grid, 256, 0, s>>>(G, X, Y, out, C, P->eig, P->st, P->Cp, prm ? prm->mode : 0, prm ? prm->rank : 0,
+                                   P->L);
+  SMSM_LAUNCH_CHECK("k_cgemm");
+  return SMSM_OK;
 }
 
 // eps schedule and report, one CTA per direction d: eps_1 = eps0_rel * (largest
@@ -478,46 +530,6 @@ __global__ void k_eps(const float* __restrict__ eig, const int* __restrict__ swe
   }
 }
 
-// W[a][b] = sum_j V[a][j] f_j conj(V[b][j]), f_j = (max(s_j, 0) + eps)^(-1/2) (IRLS) or
-// [s_j among the C - rank smallest] (NULLSPACE).  16 x 16 output tiles, K tiles of 16.
-__global__ void __launch_bounds__(256) k_weights(const float2* __restrict__ V, const float* __restrict__ eig,
-                                                 const SolverState* __restrict__ st, float2* __restrict__ W, int C,
-                                                 int Cp, int mode, int rank, int L) {
-  __shared__ float f[SMSM_MAX_C];
-  __shared__ float2 As[CG_T][CG_T + 1];
-  __shared__ float2 Bs[CG_T][CG_T + 1];
-  const int l = blockIdx.z;  // flat (direction, slice)
-  const float* s = eig + (size_t)l * Cp;
-  const double eps = st[l / L].eps;
-  for (int j = threadIdx.x; j < C; j += blockDim.x) {
-    if (mode == SMSM_MODE_NULLSPACE) {
-      int rk = 0;
-      const float sj = s[j];
-      for (int k = 0; k < C; ++k) rk += (s[k] < sj) || (s[k] == sj && k < j);
-      f[j] = rk < C - rank ? 1.f : 0.f;
-    } else {
-      f[j] = (float)(1.0 / sqrt(fmax((double)s[j], 0.0) + eps));
-    }
-  }
-  __syncthreads();
-  const float2* Vl = V + (size_t)l * C * C;
-  const int ty = threadIdx.x / CG_T, tx = threadIdx.x % CG_T;
-  const int a0 = blockIdx.y * CG_T, b0 = blockIdx.x * CG_T;
-  float2 acc = cmk(0.f, 0.f);
-  for (int k0 = 0; k0 < C; k0 += CG_T) {
-    const int ka = k0 + tx;
-    // As[row a][k] = V[a][k] f_k ; Bs[k][col b] = conj(V[b][k])  (loads coalesced along k)
-    As[ty][tx] = (a0 + ty < C && ka < C) ? cscale(Vl[(size_t)(a0 + ty) * C + ka], f[ka]) : cmk(0.f, 0.f);
-    Bs[tx][ty] = (b0 + ty < C && ka < C) ? conjf2(Vl[(size_t)(b0 + ty) * C + ka]) : cmk(0.f, 0.f);
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < CG_T; ++k) cfma(acc, As[ty][k], Bs[k][tx]);
-    __syncthreads();
-  }
-  if (a0 + ty < C && b0 + tx < C) W[((size_t)l * C + a0 + ty) * C + b0 + tx] = acc;
-}
-
-
 // the two-CTA solver holds all of G in one CTA's shared memory (C up to 168)
 bool eig_pair_supported(int Cp) {
   const int nh = (Cp / 2 + 1) & ~1;
@@ -552,23 +564,17 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   // warm start from the previous outer iteration's eigenvectors (same solve)
   const int warm = (outer > 0 && !prm->eig_cold) ? 1 : 0;
   if (T) T->begin(SMSM_STAGE_EIG);
+  smsm_status sg;
   if (P->eig_cluster) {
     // one-sided Jacobi on A = G V_prev (the congruence's first product) or on G itself
-    if (warm) {
-      dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-      k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
-      SMSM_LAUNCH_CHECK("k_congruence");
-    }
+    if (warm && (sg = launch_cgemm<SG_GV>(P, G, P->V, nullptr, P->Gw, prm, s))) return sg;
     const float tol = prm->eig_tol > 0.f ? prm->eig_tol : 2e-6f;
     smsm_status st = launch_eig_cluster(P, G, warm ? P->Gw : nullptr, msw, tol, 1e-12f, s);
     if (st) return st;
   } else {
   if (warm) {
-    dim3 gc((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, nullptr, P->Gw, C, 0);
-    SMSM_LAUNCH_CHECK("k_congruence");
-    k_congruence<<<gc, CG_T * CG_T, 0, s>>>(G, P->V, P->Gw, P->Gw2, C, 1);
-    SMSM_LAUNCH_CHECK("k_congruence");
+    if ((sg = launch_cgemm<SG_GV>(P, G, P->V, nullptr, P->Gw, prm, s))) return sg;
+    if ((sg = launch_cgemm<SG_VHT>(P, nullptr, P->V, P->Gw, P->Gw2, prm, s))) return sg;
   }
   // absolute floor of the rotation test, relative to the largest diagonal entry: far below
   // every eigenvalue W resolves (the weight changes by about delta / (2 eps) for an
@@ -583,22 +589,15 @@ smsm_status launch_eig_weights(const smsm_plan_s* P, const double2* G, int outer
   }
   if (T) T->end(SMSM_STAGE_EIG);
   if (T) T->begin(SMSM_STAGE_VAPPLY);
-  {
-    dim3 gn((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-    k_ns<<<gn, CG_T * CG_T, 0, s>>>(P->V, nullptr, P->Gw, C, 0);
-    SMSM_LAUNCH_CHECK("k_ns");
-    k_ns<<<gn, CG_T * CG_T, 0, s>>>(P->V, P->Gw, P->Gw2, C, 1);
-    SMSM_LAUNCH_CHECK("k_ns");
-    SMSM_CUDA_TRY(cudaMemcpyAsync(P->V, P->Gw2, sizeof(float2) * (size_t)P->LD * C * C, cudaMemcpyDeviceToDevice, s));
-  }
+  if ((sg = launch_cgemm<SG_VHV>(P, nullptr, P->V, nullptr, P->Gw, prm, s))) return sg;
+  if ((sg = launch_cgemm<SG_NS>(P, nullptr, P->V, P->Gw, P->Gw2, prm, s))) return sg;
+  SMSM_CUDA_TRY(cudaMemcpyAsync(P->V, P->Gw2, sizeof(float2) * (size_t)P->LD * C * C, cudaMemcpyDeviceToDevice, s));
   if (T) T->end(SMSM_STAGE_VAPPLY);
   if (T) T->begin(SMSM_STAGE_WEIGHTS);
   k_eps<<<P->D, 256, 0, s>>>(P->eig, P->sweeps, P->st, P->rep, P->L, C, Cp, outer, prm->eps0_rel, prm->eta,
                              prm->eps_min_rel);
   SMSM_LAUNCH_CHECK("k_eps");
-  dim3 gw((C + CG_T - 1) / CG_T, (C + CG_T - 1) / CG_T, P->LD);
-  k_weights<<<gw, CG_T * CG_T, 0, s>>>(P->V, P->eig, P->st, P->Wf, C, Cp, prm->mode, prm->rank, P->L);
-  SMSM_LAUNCH_CHECK("k_weights");
+  if ((sg = launch_cgemm<SG_W>(P, nullptr, P->V, nullptr, P->Wf, prm, s))) return sg;
   if (T) T->end(SMSM_STAGE_WEIGHTS);
   return SMSM_OK;
 }
