@@ -196,8 +196,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
   const int nblk = (nh / 2) * (nh + 1);
   const float inv_n1 = 1.f / (float)(nh + 1);
   float4* rot = reinterpret_cast<float4*>(regb);
-  int* rp = reinterpret_cast<int*>(rot + half);
-  int* rq = rp + half;
+  int2* rpq = reinterpret_cast<int2*>(rot + half);  // (p, q) of every pair of the round
   const uint32_t r_buf = cl_map(rbuf, 1), r_hdr = cl_map(hdr, 1);
   const uint32_t r_full0 = cl_map(&full_b[0], 1), r_full1 = cl_map(&full_b[1], 1);
   long msg = 0;  // messages sent to rank 1 (counted by the sender warp)
@@ -267,8 +266,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
     for (int round = 0; round < Cp - 1; ++round) {
       if (tid < half) {
         const int p = min(pa, pb), q = max(pa, pb);
-        rp[tid] = p;
-        rq[tid] = q;
+        rpq[tid] = make_int2(p, q);
         const float a = g[p * ld + p].x, d = g[q * ld + q].x;
         const float2 b = g[p * ld + q];
         const float babs = hypotf(b.x, b.y);
@@ -295,7 +293,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
         if (k1 < 0) continue;
         const float4 J1 = rot[k1];
         const bool id1 = is_ident(J1);
-        const int p1 = rp[k1], q1 = rq[k1];
+        const int2 pq1 = rpq[k1];
+        const int p1 = pq1.x, q1 = pq1.y;
         if (k2 == k1) {
           if (id1) continue;
           const float a = g[p1 * ld + p1].x, d = g[q1 * ld + q1].x;
@@ -309,7 +308,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(1024)
         }
         const float4 J2 = rot[k2];
         if (id1 && is_ident(J2)) continue;
-        const int p2 = rp[k2], q2 = rq[k2];
+        const int2 pq2 = rpq[k2];
+        const int p2 = pq2.x, q2 = pq2.y;
         const float2 B00 = g[p1 * ld + p2], B01 = g[p1 * ld + q2];
         // row q1 times conj(e1)
         const float2 e1c = cmk(J1.z, -J1.w);
