@@ -252,9 +252,12 @@ def stage_work(cfg, D, sweeps):
         "column": ("alu", D * col),
         "band": ("alu", D * 8 * L * nband * Ns * Ns * R2 * R2),
         "gram": ("alu", D * 8 * L * P * C * (C + 1) / 2),
-        "eig": ("alu", D * L * sweeps * (Cp - 1) * (half * (half + 1) / 2) * 96),
-        # rotation replay on V's rows, then the Newton-Schulz step (two C x C complex products)
-        "vapply": ("alu", D * L * (sweeps * (Cp - 1) * half * C * 18 + 2 * 8 * C ** 3)),
+        # every round: the 2x2 blocks of G (96 flops each) and the rotated column pairs of V
+        # (18 flops per row and pair); plus the warm start's two C x C complex products
+        "eig": ("alu", D * L * (sweeps * (Cp - 1) * ((half * (half + 1) / 2) * 96 + half * C * 18)
+                                + 2 * 8 * C ** 3)),
+        # the Newton-Schulz step (two C x C complex products)
+        "vapply": ("alu", D * L * 2 * 8 * C ** 3),
         "rowfft_inv": ("hbm", D * 2 * 8 * B * NN),
         "rowfft_fwd": ("hbm", D * 2 * 8 * B * NN),
         "cg": ("hbm", D * 9 * 8 * B * NN),

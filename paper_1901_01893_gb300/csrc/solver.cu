@@ -648,11 +648,11 @@ static cudaError_t repoint_group(GroupExec& ge, const void* const* ys, void* con
   return e;
 }
 
-// the instantiated group graph of this call (built on first use); nullptr when it cannot
-// be built, and the call then falls back to one graph launch per group on forked streams
+// the instantiated group graph of this call (built on first use) or nullptr when it cannot
+// be built (the call then falls back to one graph launch per group on forked streams); the
+// caller holds g_group_mu until it has launched it, so no other call can evict it meanwhile
 static cudaGraphExec_t group_exec(int n, smsm_plan_s* const* plans, const void* const* ys, void* const* xs,
                                   int warm) {
-  std::lock_guard<std::mutex> lock(g_group_mu);
   for (size_t i = 0; i < g_groups.size(); ++i) {
     GroupExec& ge = g_groups[i];
     if ((int)ge.plans.size() != n || ge.warm != warm) continue;
@@ -692,9 +692,16 @@ smsm_status solver_reconstruct_groups(int n, smsm_plan_s* const* plans, const vo
   for (int k = 0; k < n; ++k)
     if ((st = ensure_graph(plans[k], prm))) return st;
   // timed solves carry their own event records: those stay on the per-group path
-  cudaGraphExec_t ex = prm->timing ? nullptr : group_exec(n, plans, ys, xs, prm->warm ? 1 : 0);
-  if (ex) {
-    SMSM_CUDA_TRY(cudaGraphLaunch(ex, s));
+  bool launched = false;
+  if (!prm->timing) {
+    std::lock_guard<std::mutex> lock(g_group_mu);
+    cudaGraphExec_t ex = group_exec(n, plans, ys, xs, prm->warm ? 1 : 0);
+    if (ex) {
+      SMSM_CUDA_TRY(cudaGraphLaunch(ex, s));
+      launched = true;
+    }
+  }
+  if (launched) {
     if (reports)
       for (int k = 0; k < n; ++k)
         if ((st = fill_report(plans[k], prm, &reports[k], s))) return st;
