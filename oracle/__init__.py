@@ -34,8 +34,8 @@ Parity status of each function (pins live in ``tests/test_oracle_pins.py``):
                               global-phase equivariance; each planted
                               mistake (weight exponent, dropped or halved
                               penalty, weight never updated) is caught
-* magnitude ................. not used by any parity check (an output
-                              convenience); parity unpinned
+* magnitude ................. the root mean square over unit-phase shots returns rho
+                              exactly (and squares average, not moduli)
 """
 from .smsm_oracle import *  # noqa: F401,F403
 from .smsm_oracle import (DEFAULT_PARAMS, adjoint, caipi_ramp, cg, fft2c, forward, gram,  # noqa: F401

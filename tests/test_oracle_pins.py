@@ -437,3 +437,19 @@ def test_global_phase_equivariance():
     x1 = O.reconstruct(y, g["sens"], 3, p)
     x2 = O.reconstruct(np.exp(0.9j) * y, g["sens"], 3, p)
     assert np.allclose(x2, np.exp(0.9j) * x1, atol=1e-10 * np.abs(x1).max())
+
+
+def test_magnitude_recovers_rho_from_unit_phase_shots():
+    # Eqs. 4-5: shot i of slice l is rho_l * phi_{l,i} with |phi| = 1, so the root mean
+    # square over the shots of |F^-1 x| is rho_l exactly, whatever the phases; and a
+    # magnitude that differs between shots averages in the square (not in the modulus).
+    rng = np.random.default_rng(5)
+    L, Ns, N = 2, 4, 16
+    rho = rng.uniform(0.1, 1.0, (L, N, N))
+    phi = np.exp(1j * rng.uniform(-np.pi, np.pi, (L, Ns, N, N)))
+    x = O.fft2c(rho[:, None] * phi)
+    assert np.allclose(O.magnitude(x), rho, rtol=0, atol=1e-12)
+    amp = np.stack([rho * (1 + k) for k in range(Ns)], axis=1)  # |m_{l,i}| = (1 + i) rho_l
+    x2 = O.fft2c(amp * phi)
+    expect = rho * np.sqrt(np.mean([(1 + k) ** 2 for k in range(Ns)]))
+    assert np.allclose(O.magnitude(x2), expect, rtol=0, atol=1e-12)
