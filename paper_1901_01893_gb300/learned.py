@@ -8,7 +8,7 @@ only draws the seeded inputs (``synth``), moves tensors and keeps the books.
 
 The paper has no learned component; the network seeds the iteration of Eq. 10
 (its first k-space, Gram and annihilating filters, Eq. 9).  The plain iteration
-remains the judge: a learned solve whose data residual ||A x - y|| / ||y|| is
+remains the arbiter: a learned solve whose data residual ||A x - y|| / ||y|| is
 above the plain method's residuals on the training set (their largest value,
 with a 5 % margin) is thrown away and the group is solved again by the plain
 method from A^H y (the fallback), and its cost is counted.
