@@ -262,9 +262,11 @@ def test_errors_do_not_abort(smsm):
     with pytest.raises(smsm.SmsmError) as e:
         plan.apply_filters(torch.zeros((L, Ns * r * r, Ns * r * r), dtype=torch.complex128, device=DEV), x, out=x)
     assert e.value.status == smsm.SMSM_ERR_ARG
-    bad = smsm.default_params(outer_iters=-1)
-    with pytest.raises(smsm.SmsmError):
-        plan.reconstruct(torch.zeros(plan.y_shape, dtype=torch.complex64, device=DEV), params=bad)
+    for bad in (smsm.default_params(outer_iters=-1), smsm.default_params(eig_tol=2.0),
+                smsm.default_params(eig_tol=-1e-6), smsm.default_params(lanes=9)):
+        with pytest.raises(smsm.SmsmError) as e:
+            plan.reconstruct(torch.zeros(plan.y_shape, dtype=torch.complex64, device=DEV), params=bad)
+        assert e.value.status == smsm.SMSM_ERR_ARG
     # an unset plan refuses to run
     p2 = smsm.Plan(L, Ns, Nc, N, r)
     with pytest.raises(smsm.SmsmError) as e:
